@@ -1,0 +1,135 @@
+/*
+ * cp_oracle.h -- plain, slow, FP64 CPU oracle of the circuit-coupled
+ * electrostatic PIC step with ion-induced secondary electron emission.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The product path never links, loads or calls
+ * this code; only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline leg (and its --impl reference arm) may use it.  It shares no
+ * code, header, table or constant with the CUDA path.
+ *
+ * Representation: particle positions are kept in cell units xi = x/dx and
+ * velocities as u = v*dt/dx (cells per step).  This is a linear change of
+ * variables of the paper's leapfrog (Sec. 2.2.2, Eqs. vel_update_main,
+ * pos_update_main); it makes the cloud-in-cell weight of a particle exactly
+ * the fractional part of xi.
+ *
+ * Species: 0 = plasma electrons, 1 = ions (loaded + beam), 2 = secondary
+ * electrons emitted by ion impact (Sec. 2.3).
+ */
+#ifndef CP_ORACLE_H
+#define CP_ORACLE_H
+
+#include <stdint.h>
+
+#define OR_SPECIES 3
+#define OR_ELECTRONS 0
+#define OR_IONS 1
+#define OR_SECONDARIES 2
+
+#define OR_MODE_STRICT 0
+#define OR_MODE_WEAK 1
+
+#define OR_CIRCUIT_SERIES_RLC 0 /* series R-L-source into the gap */
+#define OR_CIRCUIT_OPEN 1       /* floating electrode: no circuit charge */
+
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_RESIDUAL (-5)
+#define OR_ERR_NONFINITE (-6)
+
+/* Philox stream tags (second key word). */
+#define OR_TAG_SEE 0x5345ULL
+#define OR_TAG_BEAM 0x4245ULL
+
+typedef struct {
+  /* gap, Sec. 2.2.1 and App. B */
+  double d;        /* electrode separation [m] */
+  double area;     /* electrode area A [m^2] */
+  double eps0;     /* vacuum permittivity [F/m] */
+  double e;        /* elementary charge [C] */
+  double m_e;      /* electron mass [kg] */
+  double m_i;      /* ion mass [kg] (singly charged) */
+  /* circuit, Sec. 2.1 and App. A (series R-L-source; see or_circuit_*) */
+  double R, L, C;  /* [Ohm], [H], [F] */
+  double V0, f, tau; /* source V_s(t) = V0 (1 - cos 2 pi f t) exp(-t/tau) / 2 */
+  double polarity; /* sign with which V_s drives the x = 0 electrode */
+  /* ion-induced SEE, Sec. 2.3 / Algorithm see_sampling_1d */
+  double gamma_coef; /* gamma(E) = min(scale*coef*sqrt(E/E_ref), gamma_max) */
+  double gamma_max;
+  double E_ref_eV;
+  double see_scale;
+  double T_emit_eV;  /* temperature of the emitted half-Maxwellian [eV] */
+  /* ion beam entering at x = d */
+  double beam_E_eV, beam_Emin_eV, beam_Emax_eV;
+  /* run */
+  double dt;       /* time step [s] */
+  double weight;   /* macroparticle weight (physical particles per macroparticle) */
+  double sigma0;   /* initial surface charge density sigma_+^{-1} [C/m^2] */
+  uint64_t seed;
+  int64_t n_cells;       /* N: nodes 0..N, phi_N = 0 */
+  int64_t circuit;       /* OR_CIRCUIT_* */
+  int64_t beam_per_step; /* beam macroparticles appended per step */
+  int64_t beam_mode;     /* 0 mono-energetic, 1 uniform in [Emin, Emax] */
+} or_params;
+
+/* Per-level diagnostics record: level n is written by the solve at t_n. */
+typedef struct {
+  int64_t step;
+  double t;
+  double V_gap;     /* phi_0^n [V] */
+  double I_circ;    /* circuit current, BDF2 derivative of the circuit charge [A] */
+  double Q_surf;    /* sigma_+^n * A [C] */
+  double Q_conv;    /* convection charge over (t_{n-1}, t_n] [C] */
+  double Q_circ;    /* Q_circ^n [C] */
+  double V_source;  /* polarity * V_s(t_n) [V] */
+  double residual;  /* backward error of the coupled solve */
+  double ion_energy_eV; /* energy of ions absorbed at x = 0 during the push */
+  double max_cfl;   /* max |u| (cells/step) over the push that produced level n */
+  double pad;
+  int64_t absorbed[2][3]; /* [electrode: 0 at x=0, 1 at x=d][species] */
+  int64_t emitted[2];     /* secondaries emitted at [x=0, x=d] */
+  int64_t injected;       /* beam ions appended */
+  int64_t n_live[3];      /* live macroparticles per species at level n */
+  int64_t conv_count;     /* Q_conv / (e*w) */
+} or_diag;
+
+typedef struct or_state or_state;
+
+/* ---- building blocks (each exported so tests can pin it) ---- */
+void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+double or_u01(uint64_t w);
+double or_source(const or_params* p, double t);
+void or_deposit(int64_t N, int64_t n, const double* xi, int64_t sign, int64_t* G);
+double or_gather(const double* E, int64_t N, double xi);
+int or_thomas(int64_t n, const double* a, const double* b, const double* c,
+              const double* r, double* x);
+int64_t or_see_count(const or_params* p, double E_ion_eV, uint64_t id, int64_t step,
+                     double* gamma_out);
+void or_see_electron(const or_params* p, uint64_t id, int64_t step, int64_t j,
+                     double* v_out, double* frac_out);
+/* Loops of the two draws above over ion ids id0..id0+n-1 (test helpers). */
+void or_see_count_batch(const or_params* p, double E_ion_eV, uint64_t id0, int64_t n,
+                        int64_t step, int64_t* counts);
+void or_see_electron_batch(const or_params* p, uint64_t id0, int64_t n, int64_t step,
+                           double* v, double* frac);
+
+/* ---- whole-gap state ---- */
+or_state* or_create(const or_params* p);
+void or_destroy(or_state* s);
+int or_set_particles(or_state* s, int32_t species, const double* xi, const double* u,
+                     const uint32_t* id, int64_t n);
+int or_step(or_state* s, int32_t mode, int64_t n_steps, double tol);
+int64_t or_level(const or_state* s);
+int64_t or_n_live(const or_state* s, int32_t species);
+int or_get_particles(const or_state* s, int32_t species, double* xi, double* u,
+                     uint32_t* id, int64_t cap);
+int or_read_grid(const or_state* s, double* phi, double* rho, double* E, int64_t* G);
+int64_t or_history_len(const or_state* s);
+int or_read_history(const or_state* s, int64_t first, int64_t n, or_diag* out);
+/* Solve one coupled field problem for a given charge grid and circuit history
+   without touching particles (the App. E/F validation cases). */
+int or_solve_fields(const or_params* p, int32_t mode, const int64_t* G, int64_t conv_count,
+                    double sigma_prev, const double* Qhist /*Q^{n-1..n-4}*/, double t,
+                    double tol, double* phi, double* E, double* out /*Q_n,sigma_n,I,resid*/);
+
+#endif

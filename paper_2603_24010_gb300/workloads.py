@@ -1,0 +1,102 @@
+"""Seeded synthetic workloads shared by the CUDA path's callers and the tests.
+
+This module holds parameter sets and seeded initial-condition draws only; it
+contains none of the PIC/SEE/circuit arithmetic.  Positions come out in cell
+units (xi = x/dx in [0, N)) and velocities in cells per step (u = v dt/dx),
+the representation both the CUDA path and the oracle take.
+
+Workloads (all synthetic; the paper's measured waveforms, SEY fits and
+injection profile are not available, so these parameter sets stand in):
+
+* ``gap_1d_fp64``: 5 mm planar vacuum gap, 256 cells, 1e4 electron/H+ pairs at
+  1 eV, n0 = 1e14 m^-3, 20 keV H+ beam of 50 macroparticles/step entering at
+  x = d, SEE yield min(0.05 sqrt(E/1 keV), 3), 2 eV emitted electrons, source
+  V0 (1-cos 2 pi f t) exp(-t/tau)/2 with V0 = 100 kV, f = 1 MHz, tau = 2 us into
+  R = 50 Ohm, L = 1 uH, C = 100 pF; dt = 1 ps, 5000 steps; FP64 particles.
+* ``gap_1d_fp32_large``: same gap with 4096 cells, 1e7 macroparticles (5e6
+  pairs), 5000 beam macroparticles/step (mono 20 keV or uniform 5-50 keV
+  depending on the seed), dt = 0.5 ps, 20000 steps; FP32 particles.
+"""
+import math
+
+import numpy as np
+
+# CODATA 2018
+E_CHARGE = 1.602176634e-19
+M_E = 9.1093837015e-31
+M_P = 1.67262192369e-27
+EPS0 = 8.8541878128e-12
+
+FP64, FP32 = 0, 1
+
+
+def _base(n_cells, n_pairs, dt, steps, beam_per_step, precision, seed=0, n0=1e14):
+    d = 5e-3
+    C = 100e-12
+    area = C * d / EPS0
+    weight = n0 * d * area / n_pairs
+    return dict(
+        d=d, area=area, eps0=EPS0, e=E_CHARGE, m_e=M_E, m_i=M_P,
+        R=50.0, L=1e-6, C=C, V0=100e3, f=1e6, tau=2e-6, polarity=-1.0,
+        gamma_coef=0.05, gamma_max=3.0, E_ref_eV=1000.0, see_scale=1.0, T_emit_eV=2.0,
+        beam_E_eV=20e3, beam_Emin_eV=5e3, beam_Emax_eV=50e3,
+        dt=dt, weight=weight, sigma0=0.0, seed=seed,
+        n_cells=n_cells, circuit=0, beam_per_step=beam_per_step, beam_mode=0,
+        n_pairs=n_pairs, T_load_eV=1.0, n0=n0, steps=steps, precision=precision,
+    )
+
+
+def gap_1d_fp64(seed=0):
+    """Small FP64 gap (256 cells, 1e4 pairs, 5000 steps)."""
+    cfg = _base(256, 10_000, 1e-12, 5000, 50, FP64, seed)
+    cfg["name"] = "gap_1d_fp64"
+    return cfg
+
+
+def gap_1d_fp32_large(seed=0):
+    """Large FP32 gap (4096 cells, 1e7 macroparticles, 20000 steps)."""
+    cfg = _base(4096, 5_000_000, 0.5e-12, 20000, 5000, FP32, seed)
+    rng = np.random.default_rng([seed, 0xBEA])
+    cfg["beam_mode"] = int(rng.integers(0, 2))  # mono-energetic or uniform 5-50 keV
+    cfg["name"] = "gap_1d_fp32_large"
+    return cfg
+
+
+def scaled(cfg, **over):
+    """Copy of a workload with some parameters replaced (weight kept unless given)."""
+    out = dict(cfg)
+    out.update(over)
+    return out
+
+
+def thermal_u(cfg, mass, T_eV):
+    """Thermal speed sqrt(e T / m) expressed in cells per step."""
+    dx = cfg["d"] / cfg["n_cells"]
+    return math.sqrt(cfg["e"] * T_eV / mass) * cfg["dt"] / dx
+
+
+def load_pairs(cfg, seed=None, n_pairs=None):
+    """Co-located electron/ion pairs, uniform in the gap, Maxwellian velocities.
+
+    Returns ``(xi, u_e, u_i)`` in FP64 cell units; ion ids are 0..n-1.
+    """
+    n = int(cfg["n_pairs"] if n_pairs is None else n_pairs)
+    N = int(cfg["n_cells"])
+    rng = np.random.default_rng([int(cfg["seed"] if seed is None else seed), 0x10AD])
+    xi = rng.random(n) * N
+    xi = np.where(xi > 0.0, xi, 1e-9)  # keep every particle strictly inside (0, N)
+    ue = rng.standard_normal(n) * thermal_u(cfg, cfg["m_e"], cfg["T_load_eV"])
+    ui = rng.standard_normal(n) * thermal_u(cfg, cfg["m_i"], cfg["T_load_eV"])
+    return xi, ue, ui
+
+
+def as_precision(xi, u, N, precision):
+    """Round a particle set to the storage precision, keeping xi inside (0, N)."""
+    if precision == FP64:
+        return np.asarray(xi, np.float64), np.asarray(u, np.float64)
+    x32 = np.asarray(xi, np.float64).astype(np.float32)
+    hi = np.nextafter(np.float32(N), np.float32(0))
+    x32 = np.minimum(x32, hi)
+    x32 = np.maximum(x32, np.float32(np.finfo(np.float32).tiny))
+    u32 = np.asarray(u, np.float64).astype(np.float32)
+    return x32.astype(np.float64), u32.astype(np.float64)
