@@ -1,0 +1,323 @@
+"""Throughput of the circuit-coupled PIC step on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path (gather, push, absorption + SEE,
+beam injection, deposit, coupled Poisson/circuit solve) over the large FP32
+1D gap workload: 4096 cells, 1e7 macroparticles at start (5e6 e-/H+ pairs),
+5000 beam ions per step, dt = 0.5 ps, strict coupling.  The metric is
+particle-steps/s = sum over timed steps of the live macroparticles pushed in
+that step / timed seconds.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the reference implementation
+of this build, written from the paper) on the host cores on a bounded sample
+of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2603_24010_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s"
+BYTES_PER_PARTICLE_STEP = {W.FP32: 16, W.FP64: 32}  # read + write of (xi, u)
+
+
+def workload(name, seed):
+    if name == "gap_1d_fp32_large":
+        return W.gap_1d_fp32_large(seed)
+    if name == "gap_1d_fp64":
+        return W.gap_1d_fp64(seed)
+    raise SystemExit("unknown workload " + name)
+
+
+def workload_desc(cfg, K, W_):
+    return ("%s: %d cells, %d e-/H+ pairs loaded, %d beam ions/step (%s), dt %.3g s, "
+            "%s particles, strict coupling; %d warm-up + %d timed steps from t = 0"
+            % (cfg["name"], cfg["n_cells"], cfg["n_pairs"], cfg["beam_per_step"],
+               "mono 20 keV" if cfg["beam_mode"] == 0 else "uniform 5-50 keV", cfg["dt"],
+               "FP32" if cfg["precision"] == W.FP32 else "FP64", W_, K))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.split(",") for l in self.file.read().strip().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- native arm
+def load_particles(cfg, seed):
+    xi, ue, ui = W.load_pairs(cfg, seed=seed)
+    N = cfg["n_cells"]
+    xe, ue = W.as_precision(xi, ue, N, cfg["precision"])
+    xI, ui = W.as_precision(xi, ui, N, cfg["precision"])
+    return xe, ue, xI, ui
+
+
+def run_native(args, rank, world):
+    import torch
+    from paper_2603_24010_gb300 import native
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    cfg = workload(args.workload, seed=args.seed + rank)
+    K, Wm = args.steps, args.warmup
+    total_steps = Wm + K
+    xe, ue, xI, ui = load_particles(cfg, cfg["seed"])
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timed region -------------------------------------
+    g = native.Gap(cfg, max_steps=total_steps + 1, stream=stream.cuda_stream)
+    g.set_particles(native.ELECTRONS, xe, ue)
+    g.set_particles(native.IONS, xI, ui)
+    g.step(0, Wm)  # includes the upload, the level-0 solve and W warm-up steps
+    native.cp_enable_timing(g.ctx, True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(0, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kms, kn = native.cp_read_timing(g.ctx)
+    per_launch_ms = native.cp_read_launch_times(g.ctx)
+    launches = native.cp_last_launch_count(g.ctx)
+    hist = g.history(Wm, K)  # rows of levels W..W+K-1: particles pushed by the timed steps
+    live = hist["n_live"].sum(axis=1)
+    psteps = int(live.sum())
+    g.close()
+
+    # ---- end-to-end through the C ABI with host buffers ---------------------
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    g2 = native.Gap(cfg, max_steps=total_steps + 1, stream=stream.cuda_stream)
+    g2.set_particles(native.ELECTRONS, xe, ue)
+    g2.set_particles(native.IONS, xI, ui)
+    g2.step(0, K)
+    h2 = native.cp_read_history(g2.ctx, 0, K + 1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_psteps = int(sum(sum(h2[k].n_live) for k in range(K)))
+    g2.close()
+    es = 4 if cfg["precision"] == W.FP32 else 8
+    h2d = (xe.size + xI.size) * 2 * es + xI.size * 4
+    d2h = (K + 1) * 208
+
+    if world > 1:
+        t = torch.tensor([ms, e2e_s * 1e3], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        c = torch.tensor([psteps, e2e_psteps], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
+        ms, e2e_ms = float(t[0]), float(t[1])
+        psteps, e2e_psteps = int(c[0]), int(c[1])
+    else:
+        e2e_ms = e2e_s * 1e3
+    peak, peak_kind = measured_peaks()
+    bpp = BYTES_PER_PARTICLE_STEP[cfg["precision"]]
+    # Roofline of the step kernel: algorithmic bytes per launch / launch time,
+    # over the launches whose particle state (xi, u) exceeds 1.5 x the 129 MB
+    # L2, so that no launch can be served from L2.
+    state = live * bpp / 2
+    sel = state > 1.5 * 129e6
+    if not sel.any():
+        sel = np.ones_like(sel)
+    n_sel = int(sel.sum())
+    sel_ms = float(np.asarray(per_launch_ms)[sel[:len(per_launch_ms)]].sum())
+    avg_launch_ms = sel_ms / n_sel
+    achieved = bpp * float(live[sel].sum()) / (sel_ms * 1e-3) / 1e9
+    return dict(cfg=cfg, ms=ms, psteps=psteps, e2e_ms=e2e_ms, e2e_psteps=e2e_psteps, h2d=h2d,
+                d2h=d2h, launches=launches, kernel_ms=kms.tolist(), kernel_n=kn.tolist(),
+                avg_launch_ms=avg_launch_ms, achieved=achieved, peak=peak, peak_kind=peak_kind,
+                clocks=clk, bpp=bpp, n_sel=n_sel, frac_psteps_above_l2=float(live[state > 129e6].sum()) / max(psteps, 1))
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_sample(cfg, K, Wm, budget_s, rate_guess=4e7):
+    """Run the FP64 oracle on a sub-sampled copy of the workload (fewer
+    macroparticles and beam ions, same physics) for Wm + K steps, sized to
+    about budget_s seconds; returns (particle-steps/s, description)."""
+    from oracle import oracle as orc
+    # average live particles of the full workload over its first steps
+    beam_fill = min(Wm + K, int(cfg["d"] / (math.sqrt(2 * 20e3 * cfg["e"] / cfg["m_i"]) * cfg["dt"])))
+    avg_live = 2 * cfg["n_pairs"] + cfg["beam_per_step"] * beam_fill / 2.0
+    frac = min(1.0, budget_s * rate_guess / max(1.0, (Wm + K) * avg_live))
+    n_pairs = max(64, int(cfg["n_pairs"] * frac))
+    beam = max(1, int(round(cfg["beam_per_step"] * frac))) if cfg["beam_per_step"] else 0
+    sub = W.scaled(cfg, n_pairs=n_pairs, beam_per_step=beam)
+    sub["weight"] = cfg["weight"] * cfg["n_pairs"] / n_pairs
+    xi, ue, ui = W.load_pairs(sub)
+    r = orc.OracleGap(sub)
+    r.set_particles(orc.ELECTRONS, xi, ue)
+    r.set_particles(orc.IONS, xi, ui)
+    if Wm:
+        r.step(orc.STRICT, Wm)
+    t0 = time.perf_counter()
+    rc = r.step(orc.STRICT, K)
+    dt = time.perf_counter() - t0
+    h = r.history()
+    psteps = int(h["n_live"][Wm:Wm + K].sum())
+    r.close()
+    desc = ("oracle (plain FP64 C, 1 thread) on the same workload sub-sampled to %d pairs and "
+            "%d beam ions/step (fraction %.4g of the macroparticles, weights scaled), %d "
+            "warm-up + %d timed steps, %.1f s, status %d" % (n_pairs, beam, frac, Wm, K, dt, rc))
+    return psteps / dt, desc
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--workload", default="gap_1d_fp32_large")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    cfg = workload(args.workload, args.seed)
+    config = {"workload": workload_desc(cfg, args.steps, args.warmup),
+              "l2": ("inputs larger than L2 for the roofline launches (particle state > 1.5 x "
+                     "129 MB); the state starts at %.0f MB and grows with the beam, no flush"
+                     % (cfg["n_pairs"] * 2 * 2 * (4 if cfg["precision"] == W.FP32 else 8) / 1e6)),
+              "parallelism": ("replicas x%d (independent seeds)" % world) if world > 1 else "1 GPU"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        value, desc = oracle_sample(cfg, args.steps, args.warmup, budget_s=120.0)
+        line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config, "impl": "reference",
+                "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
+                                 "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_native(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, desc = oracle_sample(cfg, 200, 3, budget_s=20.0)
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": desc}
+    K = args.steps
+    value = r["psteps"] / (r["ms"] * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": r["ms"] / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if r["cfg"]["precision"] == W.FP32 else "f64", "data": "synthetic",
+        "config": config,
+        "e2e": {"value": r["e2e_psteps"] / (r["e2e_ms"] * 1e-3), "unit": "particle-steps/s",
+                "h2d_bytes_per_step": r["h2d"] / K, "d2h_bytes_per_step": r["d2h"] / K},
+        "gpu_launches": r["launches"],
+        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
+                     "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": None,
+                     "kernel": "k_step", "peak_source": r["peak_kind"],
+                     "avg_launch_ms": r["avg_launch_ms"], "launches_used": r["n_sel"],
+                     "bytes_per_particle_step": r["bpp"]},
+        "clocks": r["clocks"],
+        "cpu_baseline": cpu,
+        "particle_steps": r["psteps"],
+        "frac_particle_steps_state_above_l2": r["frac_psteps_above_l2"],
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,734 @@
+// cp_api.cu -- host side of the C ABI declared in include/cp.h.
+//
+// The context owns its device buffers (cudaMalloc at the first step call,
+// once the particle counts are known), issues every kernel on the caller's
+// stream, and replays a captured CUDA graph of `compact_every` step launches
+// plus one removal launch whenever a call covers that many steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "cp_device.cuh"
+
+namespace cpk {
+size_t step_smem_bytes(int N, int precision);
+cudaError_t step_configure(int precision, size_t smem);
+cudaError_t step_occupancy(int precision, size_t smem, int* blocks_per_sm);
+cudaError_t step_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
+                        int do_push, int mode, double tol);
+cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t st);
+cudaError_t fill_launch(int precision, void* p, int64_t n, double v, cudaStream_t st);
+}  // namespace cpk
+
+using cpk::kSpecies;
+
+struct cp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  cpk::DevParams hp{};
+  cpk::DevParams* dP = nullptr;
+  cpk::DevState* dS = nullptr;
+  int precision = CP_FP64;
+  int N = 0;
+  size_t es = 8;
+  int64_t cap_req[kSpecies] = {0, 0, 0};
+  int64_t cap[kSpecies] = {0, 0, 0};
+  void* buf_xi[2][kSpecies] = {};
+  void* buf_u[2][kSpecies] = {};
+  uint32_t* buf_id[2] = {nullptr, nullptr};
+  long long* G = nullptr;
+  long long* Glast = nullptr;
+  void* Epad = nullptr;
+  double* phi = nullptr;
+  double* E64 = nullptr;
+  cpk::AbsRec* abs = nullptr;
+  cp_diag* hist = nullptr;
+  int64_t hist_rows = 0;
+  int grid = 0;
+  size_t smem = 0;
+  bool initialized = false;
+  int compact_every = 64;
+  int since_compact = 0;
+  int64_t max_steps = 0;
+  double sigma0 = 0.0;
+  // particles staged on the host until the first step
+  std::vector<double> hx[kSpecies], hu[kSpecies];
+  std::vector<uint32_t> hid;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  double gtol[2] = {0.0, 0.0};
+  int64_t launches = 0;
+  bool timing = false;
+  double t_ms[2] = {0.0, 0.0};
+  int64_t t_n[2] = {0, 0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<double> last_step_ms;
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CP_OK : CP_ERR_CUDA; }
+
+#define CP_TRY(expr)                       \
+  do {                                     \
+    const int _rc = (expr);                \
+    if (_rc != CP_OK) return _rc;          \
+  } while (0)
+#define CP_CUDA(expr) CP_TRY(cuda_rc(expr))
+
+int64_t round4(int64_t n) { return (n + 3) & ~int64_t(3); }
+
+cpk::Bufs make_bufs(const cp_ctx* c) {
+  cpk::Bufs B;
+  B.P = c->dP;
+  B.S = c->dS;
+  B.G = c->G;
+  B.Glast = c->Glast;
+  B.Epad = c->Epad;
+  B.phi = c->phi;
+  B.E64 = c->E64;
+  B.abs = c->abs;
+  B.hist = c->hist;
+  B.hist_rows = c->hist_rows;
+  return B;
+}
+
+void free_all(cp_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    for (int s = 0; s < kSpecies; ++s) {
+      cudaFree(c->buf_xi[b][s]);
+      cudaFree(c->buf_u[b][s]);
+      c->buf_xi[b][s] = c->buf_u[b][s] = nullptr;
+    }
+    cudaFree(c->buf_id[b]);
+    c->buf_id[b] = nullptr;
+  }
+  cudaFree(c->G);
+  cudaFree(c->Glast);
+  cudaFree(c->Epad);
+  cudaFree(c->phi);
+  cudaFree(c->E64);
+  cudaFree(c->abs);
+  cudaFree(c->hist);
+  cudaFree(c->dP);
+  cudaFree(c->dS);
+  for (int m = 0; m < 2; ++m)
+    if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
+int alloc(void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return CP_ERR_OOM;
+  }
+  return CP_OK;
+}
+
+// Allocate the stores, upload the staged particles and solve level 0.
+int initialize(cp_ctx* c, int mode, double tol) {
+  const cpk::DevParams& P = c->hp;
+  int64_t n[kSpecies];
+  for (int s = 0; s < kSpecies; ++s) n[s] = static_cast<int64_t>(c->hx[s].size());
+  const int64_t B = P.beam_per_step;
+  const int64_t K = c->compact_every;
+  const int64_t ions_ever = n[1] + B * c->max_steps;
+  const int64_t def[kSpecies] = {round4(n[0]) + 4 * K + 64, round4(ions_ever) + 4 * K + 64,
+                                 std::max<int64_t>(65536, round4(ions_ever + n[2]) + 4 * K + 64)};
+  for (int s = 0; s < kSpecies; ++s) {
+    c->cap[s] = round4(c->cap_req[s] > 0 ? c->cap_req[s] : def[s]);
+    if (n[s] > c->cap[s]) return CP_ERR_CAPACITY;
+    c->hp.cap[s] = c->cap[s];
+  }
+  for (int b = 0; b < 2; ++b) {
+    for (int s = 0; s < kSpecies; ++s) {
+      CP_TRY(alloc(&c->buf_xi[b][s], c->es * c->cap[s]));
+      CP_TRY(alloc(&c->buf_u[b][s], c->es * c->cap[s]));
+      CP_CUDA(cpk::fill_launch(c->precision, c->buf_xi[b][s], c->cap[s], -1.0, c->stream));
+      CP_CUDA(cudaMemsetAsync(c->buf_u[b][s], 0, c->es * c->cap[s], c->stream));
+    }
+    CP_TRY(alloc(reinterpret_cast<void**>(&c->buf_id[b]), sizeof(uint32_t) * c->cap[1]));
+  }
+  // upload in store precision
+  for (int s = 0; s < kSpecies; ++s) {
+    if (!n[s]) continue;
+    if (c->precision == CP_FP32) {
+      std::vector<float> fx(n[s]), fu(n[s]);
+      for (int64_t k = 0; k < n[s]; ++k) {
+        fx[k] = static_cast<float>(c->hx[s][k]);
+        fu[k] = static_cast<float>(c->hu[s][k]);
+      }
+      CP_CUDA(cudaMemcpyAsync(c->buf_xi[0][s], fx.data(), 4 * n[s], cudaMemcpyHostToDevice, c->stream));
+      CP_CUDA(cudaMemcpyAsync(c->buf_u[0][s], fu.data(), 4 * n[s], cudaMemcpyHostToDevice, c->stream));
+      CP_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+      CP_CUDA(cudaMemcpyAsync(c->buf_xi[0][s], c->hx[s].data(), 8 * n[s], cudaMemcpyHostToDevice, c->stream));
+      CP_CUDA(cudaMemcpyAsync(c->buf_u[0][s], c->hu[s].data(), 8 * n[s], cudaMemcpyHostToDevice, c->stream));
+      CP_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  }
+  uint32_t id_base = 0;
+  if (n[1]) {
+    CP_CUDA(cudaMemcpyAsync(c->buf_id[0], c->hid.data(), 4 * n[1], cudaMemcpyHostToDevice, c->stream));
+    for (uint32_t v : c->hid) id_base = std::max<uint32_t>(id_base, v + 1u);
+  }
+  if (static_cast<double>(id_base) + static_cast<double>(B) * c->max_steps > 4294967295.0)
+    return CP_ERR_ARG;  // ion ids must stay within uint32
+
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->G), sizeof(long long) * (c->N + 1)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->Glast), sizeof(long long) * (c->N + 1)));
+  CP_TRY(alloc(&c->Epad, c->es * (c->N + 2)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->phi), sizeof(double) * (c->N + 1)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->E64), sizeof(double) * c->N));
+  c->hist_rows = c->max_steps + 1;
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->hist), sizeof(cp_diag) * c->hist_rows));
+  CP_CUDA(cudaMemsetAsync(c->G, 0, sizeof(long long) * (c->N + 1), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->Glast, 0, sizeof(long long) * (c->N + 1), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->Epad, 0, c->es * (c->N + 2), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->hist, 0, sizeof(cp_diag) * c->hist_rows, c->stream));
+
+  // launch shape: persistent grid of resident CTAs
+  c->smem = cpk::step_smem_bytes(c->N, c->precision);
+  CP_CUDA(cpk::step_configure(c->precision, c->smem));
+  int per_sm = 0, sms = 0;
+  CP_CUDA(cpk::step_occupancy(c->precision, c->smem, &per_sm));
+  CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  if (per_sm < 1) return CP_ERR_ARG;
+  c->grid = per_sm * sms;
+  c->hp.abs_cap = 4096;
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->abs),
+               sizeof(cpk::AbsRec) * static_cast<size_t>(c->grid) * c->hp.abs_cap));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->dP), sizeof(cpk::DevParams)));
+  CP_CUDA(cudaMemcpyAsync(c->dP, &c->hp, sizeof(cpk::DevParams), cudaMemcpyHostToDevice, c->stream));
+
+  cpk::DevState S;
+  std::memset(&S, 0, sizeof(S));
+  for (int s = 0; s < kSpecies; ++s) {
+    S.xi[s] = c->buf_xi[0][s];
+    S.u[s] = c->buf_u[0][s];
+    S.xi_alt[s] = c->buf_xi[1][s];
+    S.u_alt[s] = c->buf_u[1][s];
+    S.n_alloc[s] = round4(n[s]);
+    S.n_proc[s] = round4(n[s]);
+    S.n_live[s] = n[s];
+  }
+  S.id = c->buf_id[0];
+  S.id_alt = c->buf_id[1];
+  S.sigma = c->sigma0;
+  S.beam_id_base = id_base;
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->dS), sizeof(cpk::DevState)));
+  CP_CUDA(cudaMemcpyAsync(c->dS, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < kSpecies; ++s) {
+    std::vector<double>().swap(c->hx[s]);
+    std::vector<double>().swap(c->hu[s]);
+  }
+  std::vector<uint32_t>().swap(c->hid);
+  c->initialized = true;
+  // deposit rho^0 and solve level 0
+  CP_CUDA(cpk::step_launch(c->precision, make_bufs(c), c->grid, c->smem, c->stream, 0, mode, tol));
+  c->launches += 1;
+  return CP_OK;
+}
+
+int read_status(cp_ctx* c) {
+  int st = 0;
+  CP_CUDA(cudaMemcpyAsync(&st, &c->dS->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+// Capture compact_every step launches plus one removal launch into a graph.
+int build_graph(cp_ctx* c, int mode, double tol) {
+  if (c->gexec[mode] && c->gtol[mode] == tol) return CP_OK;
+  if (c->gexec[mode]) {
+    cudaGraphExecDestroy(c->gexec[mode]);
+    c->gexec[mode] = nullptr;
+  }
+  const cpk::Bufs B = make_bufs(c);
+  cudaGraph_t g = nullptr;
+  CP_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < c->compact_every && e == cudaSuccess; ++k)
+    e = cpk::step_launch(c->precision, B, c->grid, c->smem, c->cap_stream, 1, mode, tol);
+  if (e == cudaSuccess) e = cpk::compact_launch(c->precision, B, c->grid, c->cap_stream);
+  const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return CP_ERR_CUDA;
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&c->gexec[mode], g, 0);
+  cudaGraphDestroy(g);
+  CP_CUDA(e3);
+  c->gtol[mode] = tol;
+  return CP_OK;
+}
+
+// Launch one kernel (0 = step, 1 = removal) between two timing events.
+int timed_launch(cp_ctx* c, int which, int mode, double tol, std::vector<std::pair<int, size_t>>* rec) {
+  const size_t k = rec->size() * 2;
+  while (c->ev_pool.size() < k + 2) {
+    cudaEvent_t e;
+    CP_CUDA(cudaEventCreate(&e));
+    c->ev_pool.push_back(e);
+  }
+  CP_CUDA(cudaEventRecord(c->ev_pool[k], c->stream));
+  const cpk::Bufs B = make_bufs(c);
+  if (which == 0)
+    CP_CUDA(cpk::step_launch(c->precision, B, c->grid, c->smem, c->stream, 1, mode, tol));
+  else
+    CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
+  CP_CUDA(cudaEventRecord(c->ev_pool[k + 1], c->stream));
+  rec->push_back({which, k});
+  return CP_OK;
+}
+
+int do_steps_timed(cp_ctx* c, int mode, int32_t n_steps, double tol) {
+  std::vector<std::pair<int, size_t>> rec;
+  rec.reserve(2 * static_cast<size_t>(n_steps) + 2);
+  for (int k = 0; k < n_steps; ++k) {
+    CP_TRY(timed_launch(c, 0, mode, tol, &rec));
+    c->launches += 1;
+    if (++c->since_compact == c->compact_every) {
+      CP_TRY(timed_launch(c, 1, mode, tol, &rec));
+      c->launches += 1;
+      c->since_compact = 0;
+    }
+  }
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  c->last_step_ms.clear();
+  for (const auto& r : rec) {
+    float ms = 0.f;
+    CP_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[r.second], c->ev_pool[r.second + 1]));
+    c->t_ms[r.first] += ms;
+    c->t_n[r.first] += 1;
+    if (r.first == 0) c->last_step_ms.push_back(ms);
+  }
+  return CP_OK;
+}
+
+int do_steps(cp_ctx* c, int mode, int32_t n_steps, double tol) {
+  if (!c || n_steps < 0 || !(tol > 0.0)) return CP_ERR_ARG;
+  CP_CUDA(cudaSetDevice(c->device));
+  c->launches = 0;
+  if (!c->initialized) CP_TRY(initialize(c, mode, tol));
+  int64_t level = 0;
+  CP_CUDA(cudaMemcpyAsync(&level, &c->dS->level, sizeof(level), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  if (level + n_steps > c->max_steps) return CP_ERR_ARG;
+  if (c->timing) {
+    CP_TRY(do_steps_timed(c, mode, n_steps, tol));
+    return read_status(c);
+  }
+  const cpk::Bufs B = make_bufs(c);
+  int left = n_steps;
+  while (left > 0) {
+    if (c->since_compact == 0 && left >= c->compact_every) {
+      CP_TRY(build_graph(c, mode, tol));
+      CP_CUDA(cudaGraphLaunch(c->gexec[mode], c->stream));
+      c->launches += c->compact_every + 1;
+      left -= c->compact_every;
+      continue;
+    }
+    CP_CUDA(cpk::step_launch(c->precision, B, c->grid, c->smem, c->stream, 1, mode, tol));
+    c->launches += 1;
+    --left;
+    if (++c->since_compact == c->compact_every) {
+      CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
+      c->launches += 1;
+      c->since_compact = 0;
+    }
+  }
+  return read_status(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see, const cp_run* run,
+              void* stream, cp_ctx** out) {
+  if (!gap || !circ || !see || !run || !out) return CP_ERR_ARG;
+  *out = nullptr;
+  if (gap->n_cells < 2 || !(gap->d > 0) || !(run->dt > 0) || !(gap->weight > 0) ||
+      !(gap->eps0 > 0) || !(gap->e > 0) || !(gap->m_e > 0) || !(gap->m_i > 0) ||
+      (run->precision != CP_FP64 && run->precision != CP_FP32) ||
+      (circ->kind != CP_CIRCUIT_SERIES_RLC && circ->kind != CP_CIRCUIT_OPEN) ||
+      see->beam_per_step < 0 || (see->beam_mode != 0 && see->beam_mode != 1) || run->max_steps < 0)
+    return CP_ERR_ARG;
+  if (circ->kind == CP_CIRCUIT_SERIES_RLC && (!(circ->C > 0) || !(circ->R >= 0) || !(circ->L >= 0) ||
+                                              !(circ->R > 0 || circ->L > 0) || !(circ->tau > 0)))
+    return CP_ERR_ARG;
+  if (!(gap->area > 0) && !(circ->C > 0)) return CP_ERR_ARG;
+  cp_ctx* c = new (std::nothrow) cp_ctx();
+  if (!c) return CP_ERR_OOM;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return CP_ERR_CUDA;
+  }
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->precision = run->precision;
+  c->es = (run->precision == CP_FP32) ? sizeof(float) : sizeof(double);
+  c->N = gap->n_cells;
+  c->compact_every = run->compact_every > 0 ? run->compact_every : 64;
+  c->max_steps = run->max_steps > 0 ? run->max_steps : 100000;
+  c->sigma0 = gap->sigma0;
+  for (int s = 0; s < kSpecies; ++s) c->cap_req[s] = run->capacity[s];
+  cpk::DevParams& P = c->hp;
+  P.N = gap->n_cells;
+  P.circuit = circ->kind;
+  P.beam_per_step = see->beam_per_step;
+  P.beam_mode = see->beam_mode;
+  P.d = gap->d;
+  P.dx = gap->d / static_cast<double>(gap->n_cells);
+  P.dt = run->dt;
+  P.area = gap->area > 0 ? gap->area : circ->C * gap->d / gap->eps0;
+  P.eps0 = gap->eps0;
+  P.e = gap->e;
+  P.m_e = gap->m_e;
+  P.m_i = gap->m_i;
+  P.weight = gap->weight;
+  P.R = circ->R;
+  P.L = circ->L;
+  P.C = circ->C;
+  P.V0 = circ->V0;
+  P.f = circ->f;
+  P.tau = circ->tau > 0 ? circ->tau : 1.0;
+  P.polarity = circ->polarity;
+  P.gamma_coef = see->gamma_coef;
+  P.gamma_max = see->gamma_max;
+  P.E_ref_eV = see->E_ref_eV > 0 ? see->E_ref_eV : 1000.0;
+  P.see_scale = see->scale;
+  P.T_emit_eV = see->T_emit_eV;
+  P.beam_E_eV = see->beam_E_eV;
+  P.beam_Emin_eV = see->beam_Emin_eV;
+  P.beam_Emax_eV = see->beam_Emax_eV;
+  P.seed = run->seed;
+  P.scale = P.e * P.weight / (P.area * P.dx * 4294967296.0);
+  const double dt = P.dt, dx = P.dx;
+  P.kappa[CP_ELECTRONS] = -P.e * dt * dt / (P.m_e * dx);
+  P.kappa[CP_IONS] = P.e * dt * dt / (P.m_i * dx);
+  P.kappa[CP_SECONDARIES] = P.kappa[CP_ELECTRONS];
+  P.see_vth = std::sqrt(P.e * P.T_emit_eV / P.m_e);
+  P.precision = run->precision;
+  *out = c;
+  return CP_OK;
+}
+
+int cp_set_particles(cp_ctx* c, int32_t species, const double* x, const double* v,
+                     const uint32_t* id, int64_t n, int32_t units) {
+  if (!c || species < 0 || species >= kSpecies || n < 0 || c->initialized ||
+      (units != CP_UNITS_CELL && units != CP_UNITS_SI) || (n > 0 && (!x || !v)))
+    return CP_ERR_ARG;
+  if (c->cap_req[species] > 0 && n > c->cap_req[species]) return CP_ERR_CAPACITY;
+  const double dx = c->hp.dx, dt = c->hp.dt;
+  const double N = static_cast<double>(c->N);
+  std::vector<double> hx(n), hu(n);
+  for (int64_t k = 0; k < n; ++k) {
+    double xi = units == CP_UNITS_SI ? x[k] / dx : x[k];
+    double u = units == CP_UNITS_SI ? v[k] * dt / dx : v[k];
+    if (!(xi > 0.0) || !(xi < N) || !std::isfinite(u)) return CP_ERR_ARG;
+    if (c->precision == CP_FP32) {
+      float f = static_cast<float>(xi);
+      if (f >= static_cast<float>(N)) f = std::nextafter(static_cast<float>(N), 0.0f);
+      if (!(f > 0.0f)) f = 1.17549435e-38f;
+      xi = f;
+      u = static_cast<float>(u);
+    }
+    hx[k] = xi;
+    hu[k] = u;
+  }
+  c->hx[species].swap(hx);
+  c->hu[species].swap(hu);
+  if (species == CP_IONS) {
+    c->hid.resize(n);
+    for (int64_t k = 0; k < n; ++k) c->hid[k] = id ? id[k] : static_cast<uint32_t>(k);
+  }
+  return CP_OK;
+}
+
+int cp_step_strict(cp_ctx* c, int32_t n_steps, double residual_tol) {
+  return do_steps(c, 0, n_steps, residual_tol);
+}
+
+int cp_step_weak(cp_ctx* c, int32_t n_steps) { return do_steps(c, 1, n_steps, 1e300); }
+
+int cp_read_scalars(cp_ctx* c, cp_diag* out) {
+  if (!c || !out) return CP_ERR_ARG;
+  if (!c->initialized) return CP_ERR_ARG;
+  CP_CUDA(cudaMemcpyAsync(out, &c->dS->cur, sizeof(cp_diag), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  return CP_OK;
+}
+
+int cp_read_history(cp_ctx* c, int64_t first, int64_t n, cp_diag* out) {
+  if (!c || !out || first < 0 || n < 0 || !c->initialized) return CP_ERR_ARG;
+  int64_t level = 0;
+  CP_CUDA(cudaMemcpyAsync(&level, &c->dS->level, sizeof(level), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  if (first + n > level + 1 || first + n > c->hist_rows) return CP_ERR_ARG;
+  if (n == 0) return CP_OK;
+  CP_CUDA(cudaMemcpyAsync(out, c->hist + first, sizeof(cp_diag) * n, cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  return CP_OK;
+}
+
+int cp_read_grid(cp_ctx* c, double* phi, double* rho, double* E, int64_t* G, int32_t n_nodes) {
+  if (!c || n_nodes != c->N + 1 || !c->initialized) return CP_ERR_ARG;
+  const int N = c->N;
+  std::vector<long long> g(N + 1);
+  if (phi) CP_CUDA(cudaMemcpyAsync(phi, c->phi, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost, c->stream));
+  if (E) CP_CUDA(cudaMemcpyAsync(E, c->E64, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaMemcpyAsync(g.data(), c->Glast, sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i <= N; ++i) {
+    if (G) G[i] = g[i];
+    if (rho) rho[i] = static_cast<double>(g[i]) * c->hp.scale;
+  }
+  return CP_OK;
+}
+
+int cp_get_particles(cp_ctx* c, int32_t species, double* xi, double* u, uint32_t* id, int64_t cap,
+                     int64_t* n) {
+  if (!c || species < 0 || species >= kSpecies || !n) return CP_ERR_ARG;
+  if (!c->initialized) {
+    const int64_t m = static_cast<int64_t>(c->hx[species].size());
+    *n = m;
+    if (m > cap) return CP_ERR_CAPACITY;
+    for (int64_t k = 0; k < m; ++k) {
+      if (xi) xi[k] = c->hx[species][k];
+      if (u) u[k] = c->hu[species][k];
+      if (id && species == CP_IONS) id[k] = c->hid[k];
+    }
+    return CP_OK;
+  }
+  cpk::DevState S;
+  CP_CUDA(cudaMemcpyAsync(&S, c->dS, sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t slots = std::min<int64_t>(S.n_alloc[species], c->cap[species]);
+  std::vector<unsigned char> bx(c->es * slots), bu(c->es * slots);
+  std::vector<uint32_t> bi(species == CP_IONS ? slots : 0);
+  if (slots) {
+    CP_CUDA(cudaMemcpyAsync(bx.data(), S.xi[species], c->es * slots, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaMemcpyAsync(bu.data(), S.u[species], c->es * slots, cudaMemcpyDeviceToHost, c->stream));
+    if (species == CP_IONS)
+      CP_CUDA(cudaMemcpyAsync(bi.data(), S.id, 4 * slots, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  int64_t m = 0;
+  for (int64_t k = 0; k < slots; ++k) {
+    double xv, uv;
+    if (c->precision == CP_FP32) {
+      xv = reinterpret_cast<const float*>(bx.data())[k];
+      uv = reinterpret_cast<const float*>(bu.data())[k];
+    } else {
+      xv = reinterpret_cast<const double*>(bx.data())[k];
+      uv = reinterpret_cast<const double*>(bu.data())[k];
+    }
+    if (!(xv > 0.0)) continue;
+    if (m < cap) {
+      if (xi) xi[m] = xv;
+      if (u) u[m] = uv;
+      if (id && species == CP_IONS) id[m] = bi[k];
+    }
+    ++m;
+  }
+  *n = m;
+  return m > cap ? CP_ERR_CAPACITY : CP_OK;
+}
+
+int cp_get_level(cp_ctx* c, int64_t* level) {
+  if (!c || !level) return CP_ERR_ARG;
+  if (!c->initialized) {
+    *level = 0;
+    return CP_OK;
+  }
+  CP_CUDA(cudaMemcpyAsync(level, &c->dS->level, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  return CP_OK;
+}
+
+// ---- checkpoint ---------------------------------------------------------------
+namespace {
+constexpr uint64_t kMagic = 0x31504b434350ULL;  // "PCCKP1"
+struct SaveHeader {
+  uint64_t magic;
+  int64_t N, precision, level, hist_n, since_compact;
+  int64_t slots[kSpecies];
+  int64_t cap[kSpecies];
+};
+}  // namespace
+
+int cp_save_state(cp_ctx* c, void* buf, size_t* len) {
+  if (!c || !len || !c->initialized) return CP_ERR_ARG;
+  cpk::DevState S;
+  CP_CUDA(cudaMemcpyAsync(&S, c->dS, sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  SaveHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kMagic;
+  h.N = c->N;
+  h.precision = c->precision;
+  h.level = S.level;
+  h.hist_n = std::min<int64_t>(S.level + 1, c->hist_rows);
+  h.since_compact = c->since_compact;
+  size_t need = sizeof(h) + sizeof(S);
+  for (int s = 0; s < kSpecies; ++s) {
+    h.slots[s] = S.n_alloc[s];
+    h.cap[s] = c->cap[s];
+    need += 2 * c->es * h.slots[s];
+  }
+  need += 4 * h.slots[1];
+  need += c->es * (c->N + 2) + sizeof(double) * (2 * c->N + 1) + sizeof(long long) * (c->N + 1);
+  need += sizeof(cp_diag) * h.hist_n;
+  if (!buf) {
+    *len = need;
+    return CP_OK;
+  }
+  if (*len < need) return CP_ERR_ARG;
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  std::memcpy(p, &S, sizeof(S));
+  p += sizeof(S);
+  auto d2h = [&](const void* src, size_t bytes) -> int {
+    if (bytes) CP_CUDA(cudaMemcpyAsync(p, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    p += bytes;
+    return CP_OK;
+  };
+  for (int s = 0; s < kSpecies; ++s) {
+    CP_TRY(d2h(S.xi[s], c->es * h.slots[s]));
+    CP_TRY(d2h(S.u[s], c->es * h.slots[s]));
+  }
+  CP_TRY(d2h(S.id, 4 * h.slots[1]));
+  CP_TRY(d2h(c->Epad, c->es * (c->N + 2)));
+  CP_TRY(d2h(c->phi, sizeof(double) * (c->N + 1)));
+  CP_TRY(d2h(c->E64, sizeof(double) * c->N));
+  CP_TRY(d2h(c->Glast, sizeof(long long) * (c->N + 1)));
+  CP_TRY(d2h(c->hist, sizeof(cp_diag) * h.hist_n));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  *len = need;
+  return CP_OK;
+}
+
+int cp_load_state(cp_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf || len < sizeof(SaveHeader) + sizeof(cpk::DevState)) return CP_ERR_ARG;
+  SaveHeader h;
+  const unsigned char* p = static_cast<const unsigned char*>(buf);
+  std::memcpy(&h, p, sizeof(h));
+  p += sizeof(h);
+  if (h.magic != kMagic || h.N != c->N || h.precision != c->precision) return CP_ERR_ARG;
+  if (!c->initialized) {
+    // allocate with the saved capacities
+    for (int s = 0; s < kSpecies; ++s) {
+      c->cap_req[s] = h.cap[s];
+      c->hx[s].clear();
+      c->hu[s].clear();
+    }
+    c->hid.clear();
+    CP_TRY(initialize(c, 0, 1e300));
+  }
+  for (int s = 0; s < kSpecies; ++s)
+    if (h.slots[s] > c->cap[s]) return CP_ERR_CAPACITY;
+  if (h.hist_n > c->hist_rows) return CP_ERR_CAPACITY;
+  cpk::DevState saved, cur;
+  std::memcpy(&saved, p, sizeof(saved));
+  p += sizeof(saved);
+  CP_CUDA(cudaMemcpyAsync(&cur, c->dS, sizeof(cur), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  // keep this context's buffers, take everything else from the checkpoint
+  cpk::DevState S = saved;
+  for (int s = 0; s < kSpecies; ++s) {
+    S.xi[s] = cur.xi[s];
+    S.u[s] = cur.u[s];
+    S.xi_alt[s] = cur.xi_alt[s];
+    S.u_alt[s] = cur.u_alt[s];
+  }
+  S.id = cur.id;
+  S.id_alt = cur.id_alt;
+  auto h2d = [&](void* dst, size_t bytes) -> int {
+    if (bytes) CP_CUDA(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    p += bytes;
+    return CP_OK;
+  };
+  for (int s = 0; s < kSpecies; ++s) {
+    CP_CUDA(cpk::fill_launch(c->precision, S.xi[s], c->cap[s], -1.0, c->stream));
+    CP_TRY(h2d(S.xi[s], c->es * h.slots[s]));
+    CP_TRY(h2d(S.u[s], c->es * h.slots[s]));
+  }
+  CP_TRY(h2d(S.id, 4 * h.slots[1]));
+  CP_TRY(h2d(c->Epad, c->es * (c->N + 2)));
+  CP_TRY(h2d(c->phi, sizeof(double) * (c->N + 1)));
+  CP_TRY(h2d(c->E64, sizeof(double) * c->N));
+  CP_TRY(h2d(c->Glast, sizeof(long long) * (c->N + 1)));
+  CP_TRY(h2d(c->hist, sizeof(cp_diag) * h.hist_n));
+  CP_CUDA(cudaMemsetAsync(c->G, 0, sizeof(long long) * (c->N + 1), c->stream));
+  CP_CUDA(cudaMemcpyAsync(c->dS, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  c->since_compact = static_cast<int>(h.since_compact);
+  return CP_OK;
+}
+
+int cp_enable_timing(cp_ctx* c, int32_t on) {
+  if (!c) return CP_ERR_ARG;
+  c->timing = (on != 0);
+  c->t_ms[0] = c->t_ms[1] = 0.0;
+  c->t_n[0] = c->t_n[1] = 0;
+  return CP_OK;
+}
+
+int cp_read_timing(cp_ctx* c, double ms[2], int64_t n[2]) {
+  if (!c || !ms || !n) return CP_ERR_ARG;
+  for (int k = 0; k < 2; ++k) {
+    ms[k] = c->t_ms[k];
+    n[k] = c->t_n[k];
+  }
+  return CP_OK;
+}
+
+int cp_read_launch_times(cp_ctx* c, double* ms, int64_t cap, int64_t* n) {
+  if (!c || !n || (cap > 0 && !ms)) return CP_ERR_ARG;
+  const int64_t m = static_cast<int64_t>(c->last_step_ms.size());
+  *n = m;
+  for (int64_t k = 0; k < m && k < cap; ++k) ms[k] = c->last_step_ms[k];
+  return m > cap ? CP_ERR_CAPACITY : CP_OK;
+}
+
+int cp_last_launch_count(cp_ctx* c, int64_t* launches) {
+  if (!c || !launches) return CP_ERR_ARG;
+  *launches = c->launches;
+  return CP_OK;
+}
+
+void cp_destroy(cp_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+const char* cp_status_str(int s) {
+  switch (s) {
+    case CP_OK: return "ok";
+    case CP_ERR_ARG: return "invalid argument or call order";
+    case CP_ERR_OOM: return "device allocation failed";
+    case CP_ERR_CUDA: return "CUDA runtime error";
+    case CP_ERR_CAPACITY: return "particle store or scratch list overflow";
+    case CP_ERR_RESIDUAL: return "strict solve did not reach the requested residual";
+    case CP_ERR_NONFINITE: return "non-finite field or circuit state";
+    case CP_ERR_TIMEOUT: return "bounded device wait gave up";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

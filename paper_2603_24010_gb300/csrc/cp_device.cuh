@@ -1,0 +1,139 @@
+// cp_device.cuh -- device-side data layout and helpers of the GB300 PIC step.
+//
+// Layout in HBM (one gap instance):
+//   particle stores, structure of arrays, one pair per species
+//     xi[s][cap_s]  position in cell units (float or double)
+//     u[s][cap_s]   velocity in cells/step
+//     id[cap_ions]  uint32 ion id (keys the SEE draws; read only for impacts)
+//   each store has a second buffer used by the periodic removal of absorbed
+//   particles; the live buffer pointers live in DevState so that captured
+//   CUDA graphs stay valid across swaps.
+//   G[N+1]        int64 charge grid being deposited for the next level
+//   Glast[N+1]    int64 charge grid of the current level (read-back copy)
+//   Epad[N+2]     half-grid field of the current level in particle precision,
+//                 padded with a copy of each end value (index k+1 = E_{k+1/2})
+//   phi[N+1], E64[N]  FP64 potential and field of the current level
+//   abs[grid*cap] per-CTA lists of ions absorbed in the current push
+//   hist[rows]    one cp_diag row per level
+//
+// A dead (absorbed) particle has xi <= 0; live particles have 0 < xi < N.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/cp.h"
+
+namespace cpk {
+
+constexpr int kSpecies = 3;
+constexpr int kThreads = 512;          // threads per CTA of the step kernel
+constexpr int kCtasPerSm = 2;          // resident CTAs per SM
+constexpr int kPerThread = 4;          // particles per thread per tile (one 16 B vector for FP32)
+constexpr uint64_t kTagSee = 0x5345ULL;
+constexpr uint64_t kTagBeam = 0x4245ULL;
+
+struct DevParams {
+  int32_t N;
+  int32_t circuit;
+  int32_t beam_per_step;
+  int32_t beam_mode;
+  double d, dx, dt, area, eps0, e, m_e, m_i, weight;
+  double R, L, C, V0, f, tau, polarity;
+  double gamma_coef, gamma_max, E_ref_eV, see_scale, T_emit_eV;
+  double beam_E_eV, beam_Emin_eV, beam_Emax_eV;
+  uint64_t seed;
+  double scale;          // rho_i = G_i * scale  [C/m^3]
+  double kappa[kSpecies];  // q dt^2 / (m dx): cells/step^2 per V/m
+  double see_vth;        // sqrt(e T_emit / m_e)
+  int64_t cap[kSpecies];
+  int32_t abs_cap;       // absorbed-ion records per CTA
+  int32_t precision;
+};
+
+// Record of one ion absorbed during the push (SEE input).
+struct AbsRec {
+  uint32_t id;
+  uint32_t electrode;
+  double u;
+};
+
+struct DevState {
+  void* xi[kSpecies];
+  void* u[kSpecies];
+  uint32_t* id;
+  void* xi_alt[kSpecies];
+  void* u_alt[kSpecies];
+  uint32_t* id_alt;
+  int64_t level;
+  int32_t pushed;
+  int32_t status;        // 0 or a CP_ERR_* code; stepping stops while non-zero
+  double sigma;          // sigma_+ at the current level
+  double Qh[4];          // Q^{n}, Q^{n-1}, Q^{n-2}, Q^{n-3}
+  int64_t n_alloc[kSpecies];  // slots in use (dead included); appends reserve here
+  int64_t n_proc[kSpecies];   // slots processed by the current push (multiple of 4)
+  int64_t n_live[kSpecies];
+  // tallies of the push in progress (cleared by the solve)
+  unsigned long long absorbed[2][kSpecies];
+  unsigned long long emitted[2];
+  unsigned long long injected;
+  long long conv_count;
+  long long ion_energy_q;     // sum of rint(256 E_eV) over ions absorbed at x = 0
+  unsigned int max_cfl_bits;  // float bits of max |u| (non-negative floats order as ints)
+  unsigned int done_ctas;     // arrival ticket for the last-CTA solve
+  unsigned long long compact_n[kSpecies];
+  unsigned int compact_done;
+  uint32_t beam_id_base;
+  cp_diag cur;                // diagnostics of the current level
+};
+
+struct Bufs {
+  const DevParams* P;
+  DevState* S;
+  long long* G;
+  long long* Glast;
+  void* Epad;
+  double* phi;
+  double* E64;
+  AbsRec* abs;
+  cp_diag* hist;
+  int64_t hist_rows;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): ten rounds of two 64x64->128
+// multiplications with Weyl-sequence key bumps.
+// ---------------------------------------------------------------------------
+struct U64x4 {
+  uint64_t w[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  U64x4 o;
+  o.w[0] = c0;
+  o.w[1] = c1;
+  o.w[2] = c2;
+  o.w[3] = c3;
+  return o;
+}
+
+// top 52 bits -> (k + 1/2) 2^-52, exact in binary64, strictly inside (0, 1)
+__device__ __forceinline__ double u01(uint64_t w) {
+  return __dmul_rn(__dadd_rn((double)(w >> 12), 0.5), 1.0 / 4503599627370496.0);
+}
+
+}  // namespace cpk

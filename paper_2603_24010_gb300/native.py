@@ -1,0 +1,327 @@
+"""Thin ctypes binding of the C ABI in ``include/cp.h`` (argument marshalling only).
+
+Every function named ``cp_*`` here calls the function of the same name in
+``libcp.so``; the class :class:`Gap` bundles them for one gap instance.  All
+arithmetic of the PIC step runs in the library's CUDA kernels.  There is no
+CPU fallback: if the library cannot be built or loaded, or no GPU is
+present, the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_RESIDUAL, ERR_NONFINITE, ERR_TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+ELECTRONS, IONS, SECONDARIES = 0, 1, 2
+FP64, FP32 = 0, 1
+SERIES_RLC, OPEN = 0, 1
+UNITS_CELL, UNITS_SI = 0, 1
+
+#: every symbol ``include/cp.h`` declares
+EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "cp_read_scalars",
+           "cp_read_history", "cp_read_grid", "cp_get_particles", "cp_get_level",
+           "cp_save_state", "cp_load_state", "cp_last_launch_count", "cp_enable_timing",
+           "cp_read_timing", "cp_read_launch_times", "cp_destroy", "cp_status_str")
+
+
+class CpError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__("%s failed: %d (%s)" % (fn, status, cp_status_str(status)))
+
+
+class cp_gap(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("d", "area", "eps0", "e", "m_e", "m_i", "weight",
+                                          "sigma0")] + [("n_cells", C.c_int32), ("pad0", C.c_int32)]
+
+
+class cp_circuit(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("R", "L", "C", "V0", "f", "tau", "polarity")] + [
+        ("kind", C.c_int32), ("pad0", C.c_int32)]
+
+
+class cp_see_beam(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("gamma_coef", "gamma_max", "E_ref_eV", "scale",
+                                          "T_emit_eV", "beam_E_eV", "beam_Emin_eV",
+                                          "beam_Emax_eV")] + [
+        ("beam_per_step", C.c_int32), ("beam_mode", C.c_int32)]
+
+
+class cp_run(C.Structure):
+    _fields_ = [("dt", C.c_double), ("seed", C.c_uint64), ("capacity", C.c_int64 * 3),
+                ("max_steps", C.c_int64), ("precision", C.c_int32), ("compact_every", C.c_int32)]
+
+
+class cp_diag(C.Structure):
+    _fields_ = [("step", C.c_int64)] + [(n, C.c_double) for n in (
+        "t", "V_gap", "I_circ", "Q_surf", "Q_conv", "Q_circ", "V_source", "residual",
+        "ion_energy_eV", "max_cfl", "pad")] + [
+        ("absorbed", (C.c_int64 * 3) * 2), ("emitted", C.c_int64 * 2), ("injected", C.c_int64),
+        ("n_live", C.c_int64 * 3), ("conv_count", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building if needed) ``libcp.so``; raises if that is impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, dp, i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)
+        u32p = C.POINTER(C.c_uint32)
+        L.cp_create.argtypes = [C.POINTER(cp_gap), C.POINTER(cp_circuit), C.POINTER(cp_see_beam),
+                                C.POINTER(cp_run), vp, C.POINTER(vp)]
+        L.cp_set_particles.argtypes = [vp, C.c_int32, dp, dp, u32p, C.c_int64, C.c_int32]
+        L.cp_step_strict.argtypes = [vp, C.c_int32, C.c_double]
+        L.cp_step_weak.argtypes = [vp, C.c_int32]
+        L.cp_read_scalars.argtypes = [vp, C.POINTER(cp_diag)]
+        L.cp_read_history.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(cp_diag)]
+        L.cp_read_grid.argtypes = [vp, dp, dp, dp, i64p, C.c_int32]
+        L.cp_get_particles.argtypes = [vp, C.c_int32, dp, dp, u32p, C.c_int64, i64p]
+        L.cp_get_level.argtypes = [vp, i64p]
+        L.cp_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.cp_load_state.argtypes = [vp, vp, C.c_size_t]
+        L.cp_last_launch_count.argtypes = [vp, i64p]
+        L.cp_enable_timing.argtypes = [vp, C.c_int32]
+        L.cp_read_timing.argtypes = [vp, dp, i64p]
+        L.cp_read_launch_times.argtypes = [vp, dp, C.c_int64, i64p]
+        L.cp_destroy.argtypes = [vp]
+        L.cp_destroy.restype = None
+        L.cp_status_str.argtypes = [C.c_int]
+        L.cp_status_str.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def library_path():
+    return _build.LIB
+
+
+def _check(fn, rc):
+    if rc != OK:
+        raise CpError(fn, rc)
+    return rc
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i64p(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def _u32p(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_uint32))
+
+
+# ---- one wrapper per C entry point -------------------------------------------
+def cp_status_str(status):
+    return lib().cp_status_str(int(status)).decode()
+
+
+def cp_create(gap, circuit, see, run, stream=None):
+    h = C.c_void_p()
+    _check("cp_create", lib().cp_create(C.byref(gap), C.byref(circuit), C.byref(see),
+                                        C.byref(run), C.c_void_p(stream or 0), C.byref(h)))
+    return h
+
+
+def cp_set_particles(ctx, species, x, v, ids=None, units=UNITS_CELL):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    if ids is not None:
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    return lib().cp_set_particles(ctx, int(species), _dp(x), _dp(v), _u32p(ids), x.size, int(units))
+
+
+def cp_step_strict(ctx, n_steps, residual_tol=1e-12):
+    return lib().cp_step_strict(ctx, int(n_steps), float(residual_tol))
+
+
+def cp_step_weak(ctx, n_steps):
+    return lib().cp_step_weak(ctx, int(n_steps))
+
+
+def cp_read_scalars(ctx):
+    d = cp_diag()
+    _check("cp_read_scalars", lib().cp_read_scalars(ctx, C.byref(d)))
+    return d
+
+
+def cp_read_history(ctx, first, n):
+    arr = (cp_diag * int(n))()
+    _check("cp_read_history", lib().cp_read_history(ctx, int(first), int(n), arr))
+    return arr
+
+
+def cp_read_grid(ctx, n_nodes):
+    phi, rho = np.zeros(n_nodes), np.zeros(n_nodes)
+    E = np.zeros(n_nodes - 1)
+    G = np.zeros(n_nodes, dtype=np.int64)
+    _check("cp_read_grid", lib().cp_read_grid(ctx, _dp(phi), _dp(rho), _dp(E), _i64p(G),
+                                              int(n_nodes)))
+    return dict(phi=phi, rho=rho, E=E, G=G)
+
+
+def cp_get_particles(ctx, species, cap=None):
+    """Live particles of one species (cell units); sized by a first query if cap is None."""
+    n = C.c_int64()
+    if cap is None:
+        rc = lib().cp_get_particles(ctx, int(species), None, None, None, 0, C.byref(n))
+        if rc not in (OK, ERR_CAPACITY):
+            _check("cp_get_particles", rc)
+        cap = n.value
+    xi, u = np.zeros(max(int(cap), 1)), np.zeros(max(int(cap), 1))
+    ids = np.zeros(max(int(cap), 1), dtype=np.uint32)
+    _check("cp_get_particles", lib().cp_get_particles(ctx, int(species), _dp(xi), _dp(u),
+                                                      _u32p(ids), int(cap), C.byref(n)))
+    m = n.value
+    return xi[:m], u[:m], (ids[:m] if species == IONS else None)
+
+
+def cp_get_level(ctx):
+    lv = C.c_int64()
+    _check("cp_get_level", lib().cp_get_level(ctx, C.byref(lv)))
+    return lv.value
+
+
+def cp_save_state(ctx):
+    n = C.c_size_t()
+    _check("cp_save_state", lib().cp_save_state(ctx, None, C.byref(n)))
+    buf = (C.c_ubyte * n.value)()
+    _check("cp_save_state", lib().cp_save_state(ctx, buf, C.byref(n)))
+    return bytes(buf)
+
+
+def cp_load_state(ctx, blob):
+    buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+    return lib().cp_load_state(ctx, buf, len(blob))
+
+
+def cp_last_launch_count(ctx):
+    n = C.c_int64()
+    _check("cp_last_launch_count", lib().cp_last_launch_count(ctx, C.byref(n)))
+    return n.value
+
+
+def cp_enable_timing(ctx, on):
+    _check("cp_enable_timing", lib().cp_enable_timing(ctx, int(bool(on))))
+
+
+def cp_read_timing(ctx):
+    ms = np.zeros(2)
+    n = np.zeros(2, dtype=np.int64)
+    _check("cp_read_timing", lib().cp_read_timing(ctx, _dp(ms), _i64p(n)))
+    return ms, n
+
+
+def cp_read_launch_times(ctx):
+    n = C.c_int64()
+    rc = lib().cp_read_launch_times(ctx, None, 0, C.byref(n))
+    if rc not in (OK, ERR_CAPACITY):
+        _check("cp_read_launch_times", rc)
+    ms = np.zeros(max(n.value, 1))
+    _check("cp_read_launch_times", lib().cp_read_launch_times(ctx, _dp(ms), n.value, C.byref(n)))
+    return ms[:n.value]
+
+
+def cp_destroy(ctx):
+    lib().cp_destroy(ctx)
+
+
+# ---- convenience ---------------------------------------------------------------
+def structs_from_config(cfg, capacity=(0, 0, 0), max_steps=None, compact_every=0):
+    """Fill the four parameter structs from a workload dictionary."""
+    gap = cp_gap(d=cfg["d"], area=cfg.get("area", 0.0), eps0=cfg["eps0"], e=cfg["e"],
+                 m_e=cfg["m_e"], m_i=cfg["m_i"], weight=cfg["weight"],
+                 sigma0=cfg.get("sigma0", 0.0), n_cells=int(cfg["n_cells"]))
+    circ = cp_circuit(R=cfg["R"], L=cfg["L"], C=cfg["C"], V0=cfg["V0"], f=cfg["f"],
+                      tau=cfg["tau"], polarity=cfg["polarity"], kind=int(cfg.get("circuit", 0)))
+    see = cp_see_beam(gamma_coef=cfg["gamma_coef"], gamma_max=cfg["gamma_max"],
+                      E_ref_eV=cfg["E_ref_eV"], scale=cfg["see_scale"], T_emit_eV=cfg["T_emit_eV"],
+                      beam_E_eV=cfg["beam_E_eV"], beam_Emin_eV=cfg["beam_Emin_eV"],
+                      beam_Emax_eV=cfg["beam_Emax_eV"], beam_per_step=int(cfg["beam_per_step"]),
+                      beam_mode=int(cfg["beam_mode"]))
+    run = cp_run(dt=cfg["dt"], seed=int(cfg["seed"]), max_steps=int(max_steps or cfg["steps"]),
+                 precision=int(cfg.get("precision", FP64)), compact_every=int(compact_every))
+    for s in range(3):
+        run.capacity[s] = int(capacity[s])
+    return gap, circ, see, run
+
+
+def current_stream():
+    """The caller's CUDA stream: torch's current stream on the current device."""
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Gap:
+    """One gap instance driven through the C ABI."""
+
+    def __init__(self, cfg, capacity=(0, 0, 0), max_steps=None, compact_every=0, stream=None):
+        self.cfg = dict(cfg)
+        self.N = int(cfg["n_cells"])
+        structs = structs_from_config(cfg, capacity, max_steps, compact_every)
+        self.ctx = cp_create(*structs, stream=current_stream() if stream is None else stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, species, xi, u, ids=None, units=UNITS_CELL):
+        _check("cp_set_particles", cp_set_particles(self.ctx, species, xi, u, ids, units))
+
+    def step(self, mode, n_steps, tol=1e-12):
+        rc = cp_step_strict(self.ctx, n_steps, tol) if mode == 0 else cp_step_weak(self.ctx, n_steps)
+        _check("cp_step_%s" % ("strict" if mode == 0 else "weak"), rc)
+
+    @property
+    def level(self):
+        return cp_get_level(self.ctx)
+
+    def scalars(self):
+        return cp_read_scalars(self.ctx)
+
+    def history(self, first=0, n=None):
+        if n is None:
+            n = self.level + 1 - first
+        arr = cp_read_history(self.ctx, first, n)
+        return diag_to_dict(arr)
+
+    def grid(self):
+        return cp_read_grid(self.ctx, self.N + 1)
+
+    def particles(self, species):
+        return cp_get_particles(self.ctx, species)
+
+
+def diag_to_dict(arr):
+    out = {}
+    n = len(arr)
+    for name, typ in cp_diag._fields_:
+        if name == "pad":
+            continue
+        if name == "absorbed":
+            out[name] = np.array([[[arr[k].absorbed[e][s] for s in range(3)] for e in range(2)]
+                                  for k in range(n)], dtype=np.int64).reshape(n, 2, 3)
+        elif name in ("emitted", "n_live"):
+            m = 2 if name == "emitted" else 3
+            out[name] = np.array([[getattr(arr[k], name)[j] for j in range(m)] for k in range(n)],
+                                 dtype=np.int64).reshape(n, m)
+        else:
+            dt = np.int64 if typ is C.c_int64 else np.float64
+            out[name] = np.array([getattr(arr[k], name) for k in range(n)], dtype=dt)
+    return out

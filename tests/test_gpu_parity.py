@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: the int64 charge grid is bit-exact on identical particle sets; per-step
+fields within 1e-5 (normwise relative) over the first 100 steps under
+identical random draws; V_gap(t) and I(t) within 0.5 % over a full run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2603_24010_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_24010_gb300 import native
+    native.lib()
+    return native
+
+
+def load_both(nat, orc, cfg, precision, n_pairs=None, max_steps=None, compact_every=0,
+              capacity=(0, 0, 0)):
+    xi, ue, ui = W.load_pairs(cfg, n_pairs=n_pairs)
+    N = cfg["n_cells"]
+    xe, ue = W.as_precision(xi, ue, N, precision)
+    xiI, ui = W.as_precision(xi, ui, N, precision)
+    g = nat.Gap(dict(cfg, precision=precision), max_steps=max_steps or cfg["steps"],
+                compact_every=compact_every, capacity=capacity)
+    g.set_particles(nat.ELECTRONS, xe, ue)
+    g.set_particles(nat.IONS, xiI, ui)
+    r = orc.OracleGap(cfg)
+    r.set_particles(orc.ELECTRONS, xe, ue)
+    r.set_particles(orc.IONS, xiI, ui)
+    return g, r
+
+
+def rel(a, b):
+    s = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / s if s > 0 else np.max(np.abs(a - b))
+
+
+# ------------------------------------------------------------------ deposit
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_cells,n_pairs", [(2, 37), (256, 10_000), (4096, 200_003)])
+def test_initial_deposit_bit_exact(nat, orc, precision, n_cells, n_pairs):
+    cfg = W.scaled(W.gap_1d_fp64(), n_cells=n_cells, n_pairs=n_pairs, beam_per_step=0)
+    g, r = load_both(nat, orc, cfg, precision, max_steps=4)
+    g.step(0, 0)  # deposit + level-0 solve
+    r.step(orc.STRICT, 0)
+    np.testing.assert_array_equal(g.grid()["G"], r.grid()["G"])
+    assert rel(g.grid()["E"], r.grid()["E"]) < 1e-12 or np.max(np.abs(r.grid()["E"])) < 1e-9
+
+
+def test_deposit_bit_exact_full_size_fp32(nat, orc):
+    """The large FP32 workload's 1e7 macroparticles, deposited once."""
+    cfg = W.gap_1d_fp32_large()
+    xi, ue, ui = W.load_pairs(cfg)
+    N = cfg["n_cells"]
+    x32, u32 = W.as_precision(xi, ue, N, 1)
+    # break the pairing so that the grid is not trivially zero
+    shifted = np.where(x32 + 0.37 < N, x32 + 0.37, x32 * 0.5)
+    shifted, _ = W.as_precision(shifted, u32, N, 1)
+    g = nat.Gap(cfg, max_steps=2)
+    g.set_particles(nat.ELECTRONS, x32, u32)
+    g.set_particles(nat.IONS, shifted, u32)
+    g.step(0, 0)
+    want = orc.deposit(N, x32, -1)
+    want = orc.deposit(N, shifted, +1, want)
+    np.testing.assert_array_equal(g.grid()["G"], want)
+
+
+# ------------------------------------------------------------ particle-free
+def test_particle_free_gap_matches_oracle_and_closed_form(nat, orc):
+    from closed_forms import rlc_closed_form
+    cfg = W.scaled(W.gap_1d_fp64(), dt=1e-11, beam_per_step=0, steps=20000)
+    g = nat.Gap(cfg, max_steps=20000)
+    g.step(0, 20000)
+    h = g.history()
+    r = orc.OracleGap(cfg)
+    assert r.step(orc.STRICT, 20000) == orc.OK
+    hr = r.history()
+    assert rel(h["V_gap"], hr["V_gap"]) < 1e-9
+    V_exact = rlc_closed_form(cfg, h["t"]) / cfg["C"]
+    assert rel(h["V_gap"], V_exact) < 2e-5
+    assert np.all(h["residual"] <= 1e-12)
+
+
+# ----------------------------------------------------- first 100 steps, FP64
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fields_first_100_steps_fp64(nat, orc, mode):
+    cfg = W.gap_1d_fp64()
+    g, r = load_both(nat, orc, cfg, 0, max_steps=200)
+    worst = 0.0
+    for k in range(100):
+        g.step(mode, 1)
+        assert r.step(mode, 1) == orc.OK
+        gg, gr = g.grid(), r.grid()
+        worst = max(worst, rel(gg["E"], gr["E"]), rel(gg["phi"], gr["phi"]))
+    assert worst < 1e-5, worst
+    hg, hr = g.history(), r.history()
+    np.testing.assert_array_equal(hg["n_live"], hr["n_live"])
+    np.testing.assert_array_equal(hg["absorbed"], hr["absorbed"])
+    assert rel(hg["V_gap"], hr["V_gap"]) < 1e-5
+    assert rel(hg["I_circ"], hr["I_circ"]) < 1e-5
+
+
+# --------------------------------------------------- first 100 steps, FP32
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fields_first_100_steps_fp32(nat, orc, mode):
+    """FP32 particles against the FP64 oracle: the error is that of FP32
+    positions (ulp(N) ~ 2^-12 cells at N = 4096) carried into the deposit."""
+    cfg = W.scaled(W.gap_1d_fp32_large(), n_pairs=200_000, beam_mode=0)
+    cfg["weight"] = cfg["n0"] * cfg["d"] * cfg["area"] / cfg["n_pairs"]
+    g, r = load_both(nat, orc, cfg, 1, max_steps=200)
+    worst = 0.0
+    for k in range(100):
+        g.step(mode, 1)
+        assert r.step(mode, 1) == orc.OK
+        worst = max(worst, rel(g.grid()["E"], r.grid()["E"]))
+    hg, hr = g.history(), r.history()
+    assert worst < 2e-3, worst
+    assert rel(hg["V_gap"], hr["V_gap"]) < 1e-3
+
+
+# ----------------------------------------------------------- full run, FP64
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_run_vgap_and_current_fp64(nat, orc, mode):
+    cfg = W.gap_1d_fp64()
+    g, r = load_both(nat, orc, cfg, 0)
+    g.step(mode, cfg["steps"])
+    assert r.step(mode, cfg["steps"]) == orc.OK
+    hg, hr = g.history(), r.history()
+    # the beam reaches the cathode and secondaries are emitted
+    assert hr["emitted"][:, 0].sum() > 100
+    assert rel(hg["V_gap"], hr["V_gap"]) < 5e-3
+    assert rel(hg["I_circ"], hr["I_circ"]) < 5e-3
+    assert rel(hg["Q_surf"], hr["Q_surf"]) < 5e-3
+
+
+# ------------------------------------------------------------- SEE parity
+def test_see_counts_and_secondaries_match_oracle(nat, orc):
+    """Ions placed just inside the cathode hit it in the first push; with the
+    same Philox keys both sides emit the same electrons."""
+    cfg = W.scaled(W.gap_1d_fp64(), beam_per_step=0, see_scale=20.0, gamma_max=3.0)
+    N = cfg["n_cells"]
+    rng = np.random.default_rng(5)
+    n = 3000
+    E_keV = rng.random(n) * 80 + 1
+    dx = cfg["d"] / N
+    ui = -np.sqrt(2 * E_keV * 1e3 * cfg["e"] / cfg["m_i"]) * cfg["dt"] / dx
+    xi = (rng.random(n) * 0.9 + 0.01) * np.abs(ui)  # every ion reaches x = 0 in one push
+    ids = rng.permutation(10 * n)[:n].astype(np.uint32)
+    g = nat.Gap(cfg, max_steps=4)
+    g.set_particles(nat.IONS, xi, ui, ids)
+    r = orc.OracleGap(cfg)
+    r.set_particles(orc.IONS, xi, ui, ids)
+    g.step(0, 1)
+    assert r.step(orc.STRICT, 1) == orc.OK
+    hg, hr = g.history(), r.history()
+    np.testing.assert_array_equal(hg["emitted"], hr["emitted"])
+    np.testing.assert_array_equal(hg["conv_count"], hr["conv_count"])
+    assert hr["emitted"][1, 0] > n
+    xg, ug, _ = g.particles(nat.SECONDARIES)
+    xr, ur, _ = r.particles(orc.SECONDARIES)
+    og, orr = np.lexsort((ug, xg)), np.lexsort((ur, xr))
+    np.testing.assert_allclose(xg[og], xr[orr], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(ug[og], ur[orr], rtol=1e-12, atol=1e-15)
+    # secondary positions come from log/cos of two libraries (ulp-level
+    # differences), so a fixed-point weight may differ by one unit
+    Gg, Gr = g.grid()["G"], r.grid()["G"]
+    assert np.max(np.abs(Gg - Gr)) <= 4
+    assert Gg[0] // 2 + Gg[1:N].sum() + Gg[N] // 2 == Gr[0] // 2 + Gr[1:N].sum() + Gr[N] // 2
+    assert hg["ion_energy_eV"][1] == pytest.approx(hr["ion_energy_eV"][1], rel=1e-12)
+
+
+# ------------------------------------------------------------- trajectory
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uniform_field_trajectory(nat, precision):
+    cfg = W.scaled(W.gap_1d_fp64(), circuit=1, sigma0=1e-9, weight=1e-30, beam_per_step=0,
+                   precision=precision)
+    N = cfg["n_cells"]
+    dx = cfg["d"] / N
+    xi0, u0 = 100.25, 0.01
+    g = nat.Gap(cfg, max_steps=300)
+    g.set_particles(nat.IONS, [xi0], [u0])
+    xs = []
+    for _ in range(200):
+        g.step(0, 1)
+        xs.append(g.particles(nat.IONS)[0][0])
+    a = cfg["e"] * cfg["sigma0"] / cfg["eps0"] / cfg["m_i"] * cfg["dt"] ** 2 / dx
+    n = np.arange(1, 201)
+    want = xi0 + u0 * n + 0.5 * a * n**2
+    tol = 1e-12 if precision == 0 else 5e-6
+    np.testing.assert_allclose(np.array(xs), want, rtol=tol)
+
+
+# ------------------------------------------------------- invariants at size
+def test_invariants_full_size_fp32(nat):
+    cfg = W.gap_1d_fp32_large()
+    xi, ue, ui = W.load_pairs(cfg)
+    N = cfg["n_cells"]
+    x32, ue32 = W.as_precision(xi, ue, N, 1)
+    _, ui32 = W.as_precision(xi, ui, N, 1)
+    g = nat.Gap(cfg, max_steps=200)
+    g.set_particles(nat.ELECTRONS, x32, ue32)
+    g.set_particles(nat.IONS, x32, ui32)
+    A, e0 = cfg["area"], cfg["eps0"]
+    dx = cfg["d"] / N
+    qw = cfg["e"] * cfg["weight"]
+    for _ in range(3):
+        g.step(0, 40)
+        d = g.scalars()
+        gr = g.grid()
+        G, E, rho = gr["G"], gr["E"], gr["rho"]
+        nl = list(d.n_live)
+        assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**32 * (nl[1] - nl[0] - nl[2])
+        sig_p = d.Q_surf / A
+        scale = abs(sig_p) + qw / A * 1e3
+        assert abs(e0 * E[0] - (sig_p + dx * rho[0] / 2)) <= 1e-9 * scale
+        q_space = dx * (rho[0] / 2 + rho[1:N].sum() + rho[N] / 2)
+        sig_m = -e0 * E[N - 1] - dx * rho[N] / 2
+        assert abs(sig_p + q_space + sig_m) <= 1e-9 * scale
+    h = g.history()
+    assert np.all(h["residual"] <= 1e-12)
+    nlh = h["n_live"]
+    np.testing.assert_array_equal(np.diff(nlh[:, 1]),
+                                  -h["absorbed"][1:, :, 1].sum(axis=1) + h["injected"][1:])
+    assert h["injected"][1] == cfg["beam_per_step"]
+
+
+# ------------------------------------------------------------ determinism
+def test_bit_identical_reruns(nat):
+    cfg = W.scaled(W.gap_1d_fp32_large(), n_pairs=300_000)
+    cfg["weight"] = cfg["n0"] * cfg["d"] * cfg["area"] / cfg["n_pairs"]
+    out = []
+    for _ in range(2):
+        xi, ue, ui = W.load_pairs(cfg)
+        xe, ue = W.as_precision(xi, ue, cfg["n_cells"], 1)
+        xI, ui = W.as_precision(xi, ui, cfg["n_cells"], 1)
+        g = nat.Gap(cfg, max_steps=300)
+        g.set_particles(nat.ELECTRONS, xe, ue)
+        g.set_particles(nat.IONS, xI, ui)
+        g.step(0, 150)
+        out.append((g.grid()["G"], g.history()["V_gap"]))
+        g.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+# ------------------------------------------------------------ checkpoint
+def test_checkpoint_resume_is_bit_identical(nat):
+    cfg = W.scaled(W.gap_1d_fp64(), steps=400)
+    xi, ue, ui = W.load_pairs(cfg)
+    a = nat.Gap(cfg, max_steps=400)
+    a.set_particles(nat.ELECTRONS, xi, ue)
+    a.set_particles(nat.IONS, xi, ui)
+    a.step(0, 100)
+    blob = nat.cp_save_state(a.ctx)
+    a.step(1, 150)
+    b = nat.Gap(cfg, max_steps=400)
+    assert nat.cp_load_state(b.ctx, blob) == nat.OK
+    assert b.level == 100
+    b.step(1, 150)
+    np.testing.assert_array_equal(a.grid()["G"], b.grid()["G"])
+    np.testing.assert_array_equal(a.history()["V_gap"], b.history()["V_gap"])
+
+
+# ---------------------------------------------------------------- errors
+def test_error_statuses(nat):
+    cfg = W.scaled(W.gap_1d_fp64(), steps=50)
+    xi, ue, ui = W.load_pairs(cfg)
+    # residual bound that no floating-point solve meets
+    g = nat.Gap(cfg, max_steps=50)
+    g.set_particles(nat.ELECTRONS, xi, ue)
+    g.set_particles(nat.IONS, xi, ui)
+    assert nat.cp_step_strict(g.ctx, 5, 1e-300) == nat.ERR_RESIDUAL
+    lv = g.level
+    assert nat.cp_step_strict(g.ctx, 5, 1e-12) == nat.ERR_RESIDUAL  # stays stopped
+    assert g.level == lv
+    # capacity overflow of the ion store when the beam appends
+    g2 = nat.Gap(cfg, max_steps=50, capacity=(0, 10_004, 0))
+    g2.set_particles(nat.ELECTRONS, xi, ue)
+    g2.set_particles(nat.IONS, xi, ui)
+    assert nat.cp_step_strict(g2.ctx, 20, 1e-12) == nat.ERR_CAPACITY
+    # invalid arguments
+    bad = dict(cfg, n_cells=1)
+    with pytest.raises(nat.CpError):
+        nat.Gap(bad)
+    g3 = nat.Gap(cfg, max_steps=5)
+    assert nat.cp_set_particles(g3.ctx, 1, [0.0], [0.0]) == nat.ERR_ARG  # on the wall
+    assert nat.cp_step_strict(g3.ctx, 6, 1e-12) == nat.ERR_ARG  # beyond max_steps
