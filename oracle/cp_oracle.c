@@ -23,7 +23,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define TWO32 4294967296.0
+#define FIX 65536.0 /* fixed-point units per macroparticle charge on the grid */
 
 /* ------------------------------------------------------------------------ */
 /* Counter-based random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw,  */
@@ -67,7 +67,7 @@ double or_source(const or_params* p, double t) {
 /* Charge deposition, App. C (linear weighting) with the boundary-node rule  */
 /* of App. E.2 (rho_0 = w_0 2q/dx, so no charge is lost at the wall).        */
 /* Fixed point: the node weights of a particle in cell i at fraction f are   */
-/* W1 = floor(f 2^32) on node i+1 and W0 = 2^32 - W1 on node i; a boundary   */
+/* W1 = floor(f 2^16) on node i+1 and W0 = 2^16 - W1 on node i; a boundary   */
 /* node receives twice its weight.  G accumulates sign(q) * weights.         */
 /* ------------------------------------------------------------------------ */
 void or_deposit(int64_t N, int64_t n, const double* xi, int64_t sign, int64_t* G) {
@@ -76,8 +76,8 @@ void or_deposit(int64_t N, int64_t n, const double* xi, int64_t sign, int64_t* G
     double fl = floor(x);
     int64_t i = (int64_t)fl;
     double f = x - fl;
-    int64_t W1 = (int64_t)floor(f * TWO32);
-    int64_t W0 = (int64_t)TWO32 - W1;
+    int64_t W1 = (int64_t)floor(f * FIX);
+    int64_t W0 = (int64_t)FIX - W1;
     if (i == 0) W0 *= 2;
     if (i + 1 == N) W1 *= 2;
     G[i] += sign * W0;
@@ -191,7 +191,7 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
   const double eps0 = p->eps0;
   const double dt = p->dt;
   const double qw = p->e * p->weight;
-  const double scale = qw / (A * dx * TWO32); /* rho_i = G_i * scale */
+  const double scale = qw / (A * dx * FIX); /* rho_i = G_i * scale */
   const double Qconv = (double)conv_count * qw;
   const double Vs = p->polarity * or_source(p, t);
   const double Q1 = Qh[0], Q2 = Qh[1], Q3 = Qh[2], Q4 = Qh[3];
@@ -603,7 +603,7 @@ int or_get_particles(const or_state* s, int32_t sp, double* xi, double* u, uint3
 }
 
 int or_read_grid(const or_state* s, double* phi, double* rho, double* E, int64_t* G) {
-  const double scale = s->p.e * s->p.weight / (s->p.area * s->dx * TWO32);
+  const double scale = s->p.e * s->p.weight / (s->p.area * s->dx * FIX);
   for (int64_t i = 0; i <= s->N; ++i) {
     if (phi) phi[i] = s->phi[i];
     if (rho) rho[i] = (double)s->G[i] * scale;

@@ -219,7 +219,7 @@ def test_invariants_full_size_fp32(nat):
         gr = g.grid()
         G, E, rho = gr["G"], gr["E"], gr["rho"]
         nl = list(d.n_live)
-        assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**32 * (nl[1] - nl[0] - nl[2])
+        assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**16 * (nl[1] - nl[0] - nl[2])
         sig_p = d.Q_surf / A
         scale = abs(sig_p) + qw / A * 1e3
         assert abs(e0 * E[0] - (sig_p + dx * rho[0] / 2)) <= 1e-9 * scale

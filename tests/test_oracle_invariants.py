@@ -6,7 +6,7 @@ loss and circuit charging all happen.  Checked at every time level:
 
 * Gauss at x = 0 (Eq. 1D_Gaussian_app) and the global Gauss balance
   sigma_+ A + Q_space + sigma_- A = 0 with sigma_- from the field at x = d;
-* the integer charge grid carries exactly 2^32 per live macroparticle;
+* the integer charge grid carries exactly 2^16 per live macroparticle;
 * particle and charge ledgers: live counts change only by absorption,
   emission and injection, and circuit-delivered charge = change of the
   surface charge - convection charge (Eq. top_plate_charge), where the
@@ -59,8 +59,8 @@ def test_conservation_on_coupled_run(orc, mode):
     for k, gr in enumerate(grids, start=1):
         G, E = gr["G"], gr["E"]
         nl = h["n_live"][k]
-        # 2^32 per live macroparticle, boundary nodes counted half
-        assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**32 * (nl[1] - nl[0] - nl[2])
+        # 2^16 per live macroparticle, boundary nodes counted half
+        assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**16 * (nl[1] - nl[0] - nl[2])
         rho = gr["rho"]
         sig_p = h["Q_surf"][k] / A
         scale = abs(sig_p) + abs(qw / A) * (nl.sum() + 1)

@@ -11,13 +11,13 @@ from paper_2603_24010_gb300 import workloads as W
 
 # ---------------------------------------------------------------- deposit
 def exact_deposit(N, xi, sign):
-    """Brute force with exact rational arithmetic: W1 = floor(frac(xi) 2^32)."""
+    """Brute force with exact rational arithmetic: W1 = floor(frac(xi) 2^16)."""
     G = [0] * (N + 1)
     for x in xi:
         fx = Fraction(float(x))
         i = math.floor(fx)
-        W1 = math.floor((fx - i) * 2**32)
-        W0 = 2**32 - W1
+        W1 = math.floor((fx - i) * 2**16)
+        W0 = 2**16 - W1
         if i == 0:
             W0 *= 2
         if i + 1 == N:
@@ -41,9 +41,9 @@ def test_deposit_conserves_charge_with_half_end_nodes(orc):
     N = 64
     xi = np.random.default_rng(1).random(1000) * N
     G = orc.deposit(N, xi, +1)
-    # each particle carries 2^32 with boundary nodes counted half
+    # each particle carries 2^16 with boundary nodes counted half
     assert G[0] % 2 == 0 and G[N] % 2 == 0
-    assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**32 * xi.size
+    assert G[0] // 2 + G[1:N].sum() + G[N] // 2 == 2**16 * xi.size
 
 
 # ----------------------------------------------------------------- gather

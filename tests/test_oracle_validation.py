@@ -46,7 +46,7 @@ def test_app_f_printed_strict_circuit_charge(orc):
     assert i0 == 120
     assert sheet_density(cfg) == pytest.approx(1.6e-19 * 2.5e7, rel=1e-15)
     G = orc.deposit(N, np.array([float(i0)]), +1)
-    assert G[i0] == 2**32 and G.sum() == 2**32
+    assert G[i0] == 2**16 and G.sum() == 2**16
     rc, phi, E, out = orc.solve_fields(cfg, orc.STRICT, G, 0, 0.0, np.zeros(4), 1000 * cfg["dt"])
     assert rc == orc.OK
     want = gold["Q_circ_strict_C"]
@@ -94,14 +94,14 @@ def test_cic_sheet_potential_is_nodally_exact(orc, xi0, sigma):
     assert rc == orc.OK
     x = np.arange(N + 1) * dx
     x0 = xi0 * dx
-    # the fixed-point weight truncates the position to 2^-32 of a cell
-    x0 = (np.floor(xi0) + np.floor((xi0 - np.floor(xi0)) * 2**32) / 2**32) * dx
+    # the fixed-point weight truncates the position to 2^-16 of a cell
+    x0 = (np.floor(xi0) + np.floor((xi0 - np.floor(xi0)) * 2**16) / 2**16) * dx
     L, e0 = cfg["d"], cfg["eps0"]
     want = sheet_density(cfg) * (L - np.maximum(x, x0)) / e0 + sigma * (L - x) / e0
     scale = (abs(sheet_density(cfg)) + abs(sigma)) * L / e0
     np.testing.assert_allclose(phi, want, rtol=0, atol=1e-10 * scale)
     # Gauss at x = 0 (Eq. 1D_Gaussian_app): eps0 E_1/2 = sigma + dx rho_0 / 2
-    rho0 = G[0] * cfg["e"] * cfg["weight"] / (cfg["area"] * dx * 2**32)
+    rho0 = G[0] * cfg["e"] * cfg["weight"] / (cfg["area"] * dx * 2**16)
     assert e0 * E[0] == pytest.approx(sigma + dx * rho0 / 2, rel=1e-12,
                                       abs=1e-14 * abs(sheet_density(cfg)))
 
