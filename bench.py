@@ -305,9 +305,11 @@ def main():
         "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
                      "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": None,
-                     "kernel": "k_step", "peak_source": r["peak_kind"],
+                     "kernel": "k_push", "peak_source": r["peak_kind"],
                      "avg_launch_ms": r["avg_launch_ms"], "launches_used": r["n_sel"],
-                     "bytes_per_particle_step": r["bpp"]},
+                     "bytes_per_particle_step": r["bpp"],
+                     "solve_avg_ms": r["kernel_ms"][1] / max(r["kernel_n"][1], 1),
+                     "removal_avg_ms": r["kernel_ms"][2] / max(r["kernel_n"][2], 1)},
         "clocks": r["clocks"],
         "cpu_baseline": cpu,
         "particle_steps": r["psteps"],

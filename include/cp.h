@@ -18,8 +18,9 @@
  * cell units: xi = x/dx in (0, N) and u = v dt/dx (cells per step).  Species
  * 0 = plasma electrons, 1 = ions (charge +e, mass m_i), 2 = secondary
  * electrons.  Every macroparticle carries the same weight.  Charge is
- * deposited as int64 fixed point (2^32 per macroparticle), so the charge grid
- * is bit-identical from run to run and independent of particle order.
+ * deposited as int64 fixed point (2^16 per macroparticle, positions resolved
+ * to 2^-16 of a cell inside the deposit), so the charge grid is bit-identical
+ * from run to run and independent of particle order.
  *
  * Memory and streams.  The library owns all device memory it allocates in
  * cp_create; the caller owns every host buffer passed in, which is only read
@@ -96,7 +97,7 @@ typedef struct {
    count = floor(gamma) + Bernoulli(gamma - floor(gamma)), speed of each
    emitted electron = sqrt(e T_emit / m_e) |N(0,1)|, normal emission.  Beam:
    beam_per_step ions per step, energy beam_E_eV (mode 0) or uniform in
-   [beam_Emin_eV, beam_Emax_eV] (mode 1). */
+   [beam_Emin_eV, beam_Emax_eV] (mode 1).  0 <= gamma_max <= 14. */
 typedef struct {
   double gamma_coef, gamma_max, E_ref_eV, scale, T_emit_eV;
   double beam_E_eV, beam_Emin_eV, beam_Emax_eV;
@@ -179,7 +180,7 @@ int cp_read_history(cp_ctx* ctx, int64_t first_step, int64_t n, cp_diag* out);
 
 /* Current level's fields: phi (N+1 nodes, V), rho (N+1 nodes, C/m^3),
    E (N edges, E[k] = E_{k+1/2}, V/m) and the int64 charge grid G (N+1;
-   rho = G e weight / (A dx 2^32)).  Any pointer may be NULL.  n_nodes must be
+   rho = G e weight / (A dx 2^16)).  Any pointer may be NULL.  n_nodes must be
    N+1.  Synchronises the stream. */
 int cp_read_grid(cp_ctx* ctx, double* phi, double* rho, double* E, int64_t* G,
                  int32_t n_nodes);
@@ -206,14 +207,14 @@ int cp_last_launch_count(cp_ctx* ctx, int64_t* launches);
 
 /* Per-launch timing.  While on != 0, step calls launch each kernel directly
    (no graph replay) bracketed by CUDA events on the context's stream, and
-   accumulate the device time of the step kernel and of the removal kernel.
-   cp_read_timing returns the totals since timing was last enabled:
-   ms[0], n[0] = step-kernel milliseconds and launches; ms[1], n[1] = the
-   same for the removal kernel. */
+   accumulate the device time of each kernel kind.  cp_read_timing returns
+   the totals since timing was last enabled: ms[k], n[k] = milliseconds and
+   launches of the particle push (k = 0), the coupled solve (k = 1) and the
+   removal of absorbed particles (k = 2). */
 int cp_enable_timing(cp_ctx* ctx, int32_t on);
-int cp_read_timing(cp_ctx* ctx, double ms[2], int64_t n[2]);
+int cp_read_timing(cp_ctx* ctx, double ms[3], int64_t n[3]);
 
-/* Device time of each step-kernel launch of the last step call made with
+/* Device time of each particle-push launch of the last step call made with
    timing on, in launch order (ms[k] for the push from level L+k, L = level
    at the start of that call).  *n receives the count; at most cap values
    are written.  Errors: CP_ERR_CAPACITY if cap < count. */

@@ -17,13 +17,17 @@
 #include "cp_device.cuh"
 
 namespace cpk {
-size_t step_smem_bytes(int N, int precision);
-cudaError_t step_configure(int precision, size_t smem);
-cudaError_t step_occupancy(int precision, size_t smem, int* blocks_per_sm);
-cudaError_t step_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
-                        int do_push, int mode, double tol);
+size_t push_smem_bytes(int N, int precision);
+size_t solve_smem_bytes(int N);
+cudaError_t kernels_configure(int precision, size_t push_smem, size_t solve_smem);
+cudaError_t push_occupancy(int precision, size_t smem, int* blocks_per_sm);
+cudaError_t push_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
+                        int do_push);
+cudaError_t solve_launch(int precision, const Bufs& B, size_t smem, cudaStream_t st, int do_push,
+                         int mode, double tol);
 cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t st);
 cudaError_t fill_launch(int precision, void* p, int64_t n, double v, cudaStream_t st);
+cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st);
 }  // namespace cpk
 
 using cpk::kSpecies;
@@ -45,14 +49,16 @@ struct cp_ctx {
   uint32_t* buf_id[2] = {nullptr, nullptr};
   long long* G = nullptr;
   long long* Glast = nullptr;
-  void* Epad = nullptr;
+  void* Epair = nullptr;
   double* phi = nullptr;
   double* E64 = nullptr;
   cpk::AbsRec* abs = nullptr;
   cp_diag* hist = nullptr;
   int64_t hist_rows = 0;
+  double* vs = nullptr;
   int grid = 0;
-  size_t smem = 0;
+  size_t smem = 0;        // push kernel
+  size_t solve_smem = 0;  // solve kernel
   bool initialized = false;
   int compact_every = 64;
   int since_compact = 0;
@@ -65,8 +71,8 @@ struct cp_ctx {
   double gtol[2] = {0.0, 0.0};
   int64_t launches = 0;
   bool timing = false;
-  double t_ms[2] = {0.0, 0.0};
-  int64_t t_n[2] = {0, 0};
+  double t_ms[3] = {0.0, 0.0, 0.0};  // push, solve, removal
+  int64_t t_n[3] = {0, 0, 0};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<double> last_step_ms;
 };
@@ -90,12 +96,13 @@ cpk::Bufs make_bufs(const cp_ctx* c) {
   B.S = c->dS;
   B.G = c->G;
   B.Glast = c->Glast;
-  B.Epad = c->Epad;
+  B.Epair = c->Epair;
   B.phi = c->phi;
   B.E64 = c->E64;
   B.abs = c->abs;
   B.hist = c->hist;
   B.hist_rows = c->hist_rows;
+  B.vs = c->vs;
   return B;
 }
 
@@ -111,11 +118,12 @@ void free_all(cp_ctx* c) {
   }
   cudaFree(c->G);
   cudaFree(c->Glast);
-  cudaFree(c->Epad);
+  cudaFree(c->Epair);
   cudaFree(c->phi);
   cudaFree(c->E64);
   cudaFree(c->abs);
   cudaFree(c->hist);
+  cudaFree(c->vs);
   cudaFree(c->dP);
   cudaFree(c->dS);
   for (int m = 0; m < 2; ++m)
@@ -185,21 +193,22 @@ int initialize(cp_ctx* c, int mode, double tol) {
 
   CP_TRY(alloc(reinterpret_cast<void**>(&c->G), sizeof(long long) * (c->N + 1)));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->Glast), sizeof(long long) * (c->N + 1)));
-  CP_TRY(alloc(&c->Epad, c->es * (c->N + 2)));
+  CP_TRY(alloc(&c->Epair, 2 * c->es * (c->N + 1)));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->phi), sizeof(double) * (c->N + 1)));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->E64), sizeof(double) * c->N));
   c->hist_rows = c->max_steps + 1;
   CP_TRY(alloc(reinterpret_cast<void**>(&c->hist), sizeof(cp_diag) * c->hist_rows));
   CP_CUDA(cudaMemsetAsync(c->G, 0, sizeof(long long) * (c->N + 1), c->stream));
   CP_CUDA(cudaMemsetAsync(c->Glast, 0, sizeof(long long) * (c->N + 1), c->stream));
-  CP_CUDA(cudaMemsetAsync(c->Epad, 0, c->es * (c->N + 2), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->Epair, 0, 2 * c->es * (c->N + 1), c->stream));
   CP_CUDA(cudaMemsetAsync(c->hist, 0, sizeof(cp_diag) * c->hist_rows, c->stream));
 
-  // launch shape: persistent grid of resident CTAs
-  c->smem = cpk::step_smem_bytes(c->N, c->precision);
-  CP_CUDA(cpk::step_configure(c->precision, c->smem));
+  // launch shape: persistent grid of resident push CTAs, one solve cluster
+  c->smem = cpk::push_smem_bytes(c->N, c->precision);
+  c->solve_smem = cpk::solve_smem_bytes(c->N);
+  CP_CUDA(cpk::kernels_configure(c->precision, c->smem, c->solve_smem));
   int per_sm = 0, sms = 0;
-  CP_CUDA(cpk::step_occupancy(c->precision, c->smem, &per_sm));
+  CP_CUDA(cpk::push_occupancy(c->precision, c->smem, &per_sm));
   CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   if (per_sm < 1) return CP_ERR_ARG;
   c->grid = per_sm * sms;
@@ -208,6 +217,8 @@ int initialize(cp_ctx* c, int mode, double tol) {
                sizeof(cpk::AbsRec) * static_cast<size_t>(c->grid) * c->hp.abs_cap));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->dP), sizeof(cpk::DevParams)));
   CP_CUDA(cudaMemcpyAsync(c->dP, &c->hp, sizeof(cpk::DevParams), cudaMemcpyHostToDevice, c->stream));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->vs), sizeof(double) * (c->hist_rows + 1)));
+  CP_CUDA(cpk::source_table_launch(c->dP, c->vs, c->hist_rows + 1, c->stream));
 
   cpk::DevState S;
   std::memset(&S, 0, sizeof(S));
@@ -234,8 +245,10 @@ int initialize(cp_ctx* c, int mode, double tol) {
   std::vector<uint32_t>().swap(c->hid);
   c->initialized = true;
   // deposit rho^0 and solve level 0
-  CP_CUDA(cpk::step_launch(c->precision, make_bufs(c), c->grid, c->smem, c->stream, 0, mode, tol));
-  c->launches += 1;
+  const cpk::Bufs B0 = make_bufs(c);
+  CP_CUDA(cpk::push_launch(c->precision, B0, c->grid, c->smem, c->stream, 0));
+  CP_CUDA(cpk::solve_launch(c->precision, B0, c->solve_smem, c->stream, 0, mode, tol));
+  c->launches += 2;
   return CP_OK;
 }
 
@@ -257,8 +270,10 @@ int build_graph(cp_ctx* c, int mode, double tol) {
   cudaGraph_t g = nullptr;
   CP_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < c->compact_every && e == cudaSuccess; ++k)
-    e = cpk::step_launch(c->precision, B, c->grid, c->smem, c->cap_stream, 1, mode, tol);
+  for (int k = 0; k < c->compact_every && e == cudaSuccess; ++k) {
+    e = cpk::push_launch(c->precision, B, c->grid, c->smem, c->cap_stream, 1);
+    if (e == cudaSuccess) e = cpk::solve_launch(c->precision, B, c->solve_smem, c->cap_stream, 1, mode, tol);
+  }
   if (e == cudaSuccess) e = cpk::compact_launch(c->precision, B, c->grid, c->cap_stream);
   const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -272,7 +287,7 @@ int build_graph(cp_ctx* c, int mode, double tol) {
   return CP_OK;
 }
 
-// Launch one kernel (0 = step, 1 = removal) between two timing events.
+// Launch one kernel (0 = push, 1 = solve, 2 = removal) between two timing events.
 int timed_launch(cp_ctx* c, int which, int mode, double tol, std::vector<std::pair<int, size_t>>* rec) {
   const size_t k = rec->size() * 2;
   while (c->ev_pool.size() < k + 2) {
@@ -283,7 +298,9 @@ int timed_launch(cp_ctx* c, int which, int mode, double tol, std::vector<std::pa
   CP_CUDA(cudaEventRecord(c->ev_pool[k], c->stream));
   const cpk::Bufs B = make_bufs(c);
   if (which == 0)
-    CP_CUDA(cpk::step_launch(c->precision, B, c->grid, c->smem, c->stream, 1, mode, tol));
+    CP_CUDA(cpk::push_launch(c->precision, B, c->grid, c->smem, c->stream, 1));
+  else if (which == 1)
+    CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_smem, c->stream, 1, mode, tol));
   else
     CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
   CP_CUDA(cudaEventRecord(c->ev_pool[k + 1], c->stream));
@@ -293,12 +310,13 @@ int timed_launch(cp_ctx* c, int which, int mode, double tol, std::vector<std::pa
 
 int do_steps_timed(cp_ctx* c, int mode, int32_t n_steps, double tol) {
   std::vector<std::pair<int, size_t>> rec;
-  rec.reserve(2 * static_cast<size_t>(n_steps) + 2);
+  rec.reserve(3 * static_cast<size_t>(n_steps) + 2);
   for (int k = 0; k < n_steps; ++k) {
     CP_TRY(timed_launch(c, 0, mode, tol, &rec));
-    c->launches += 1;
+    CP_TRY(timed_launch(c, 1, mode, tol, &rec));
+    c->launches += 2;
     if (++c->since_compact == c->compact_every) {
-      CP_TRY(timed_launch(c, 1, mode, tol, &rec));
+      CP_TRY(timed_launch(c, 2, mode, tol, &rec));
       c->launches += 1;
       c->since_compact = 0;
     }
@@ -334,12 +352,13 @@ int do_steps(cp_ctx* c, int mode, int32_t n_steps, double tol) {
     if (c->since_compact == 0 && left >= c->compact_every) {
       CP_TRY(build_graph(c, mode, tol));
       CP_CUDA(cudaGraphLaunch(c->gexec[mode], c->stream));
-      c->launches += c->compact_every + 1;
+      c->launches += 2 * c->compact_every + 1;
       left -= c->compact_every;
       continue;
     }
-    CP_CUDA(cpk::step_launch(c->precision, B, c->grid, c->smem, c->stream, 1, mode, tol));
-    c->launches += 1;
+    CP_CUDA(cpk::push_launch(c->precision, B, c->grid, c->smem, c->stream, 1));
+    CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_smem, c->stream, 1, mode, tol));
+    c->launches += 2;
     --left;
     if (++c->since_compact == c->compact_every) {
       CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
@@ -362,7 +381,8 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
       !(gap->eps0 > 0) || !(gap->e > 0) || !(gap->m_e > 0) || !(gap->m_i > 0) ||
       (run->precision != CP_FP64 && run->precision != CP_FP32) ||
       (circ->kind != CP_CIRCUIT_SERIES_RLC && circ->kind != CP_CIRCUIT_OPEN) ||
-      see->beam_per_step < 0 || (see->beam_mode != 0 && see->beam_mode != 1) || run->max_steps < 0)
+      see->beam_per_step < 0 || (see->beam_mode != 0 && see->beam_mode != 1) || run->max_steps < 0 ||
+      !(see->gamma_max >= 0.0 && see->gamma_max <= 14.0))
     return CP_ERR_ARG;
   if (circ->kind == CP_CIRCUIT_SERIES_RLC && (!(circ->C > 0) || !(circ->R >= 0) || !(circ->L >= 0) ||
                                               !(circ->R > 0 || circ->L > 0) || !(circ->tau > 0)))
@@ -413,12 +433,30 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.beam_Emin_eV = see->beam_Emin_eV;
   P.beam_Emax_eV = see->beam_Emax_eV;
   P.seed = run->seed;
-  P.scale = P.e * P.weight / (P.area * P.dx * 4294967296.0);
+  P.scale = P.e * P.weight / (P.area * P.dx * cpk::kFix);
   const double dt = P.dt, dx = P.dx;
   P.kappa[CP_ELECTRONS] = -P.e * dt * dt / (P.m_e * dx);
   P.kappa[CP_IONS] = P.e * dt * dt / (P.m_i * dx);
   P.kappa[CP_SECONDARIES] = P.kappa[CP_ELECTRONS];
   P.see_vth = std::sqrt(P.e * P.T_emit_eV / P.m_e);
+  P.a21 = 9.0 * P.L / (4.0 * dt * dt) + 3.0 * P.R / (2.0 * dt);
+  P.alpha = dx * dx * P.scale / P.eps0;
+  P.g_strict = P.a21 > 0 ? 1.0 / P.a21 : 0.0;
+  P.g_weak = 1.0 / (P.a21 + 1.0 / P.C);
+  P.gam_strict = P.g_strict * dx / (P.eps0 * P.area);
+  P.inv_den_strict = 1.0 / (1.0 + static_cast<double>(P.N) * P.gam_strict);
+  P.dx_eps0 = dx / P.eps0;
+  P.inv_A = 1.0 / P.area;
+  P.inv_dx = 1.0 / dx;
+  P.inv_2dt = 1.0 / (2.0 * dt);
+  P.L4dt2 = P.L / (4.0 * dt * dt);
+  P.R2dt = P.R / (2.0 * dt);
+  for (int s = 0; s < kSpecies; ++s) {
+    P.kap_d[0][s] = 0.5 * P.kappa[s];
+    P.kap_d[1][s] = P.kappa[s];
+    P.kap_f[0][s] = static_cast<float>(P.kap_d[0][s]);
+    P.kap_f[1][s] = static_cast<float>(P.kap_d[1][s]);
+  }
   P.precision = run->precision;
   *out = c;
   return CP_OK;
@@ -588,7 +626,7 @@ int cp_save_state(cp_ctx* c, void* buf, size_t* len) {
     need += 2 * c->es * h.slots[s];
   }
   need += 4 * h.slots[1];
-  need += c->es * (c->N + 2) + sizeof(double) * (2 * c->N + 1) + sizeof(long long) * (c->N + 1);
+  need += 2 * c->es * (c->N + 1) + sizeof(double) * (2 * c->N + 1) + sizeof(long long) * (c->N + 1);
   need += sizeof(cp_diag) * h.hist_n;
   if (!buf) {
     *len = need;
@@ -610,7 +648,7 @@ int cp_save_state(cp_ctx* c, void* buf, size_t* len) {
     CP_TRY(d2h(S.u[s], c->es * h.slots[s]));
   }
   CP_TRY(d2h(S.id, 4 * h.slots[1]));
-  CP_TRY(d2h(c->Epad, c->es * (c->N + 2)));
+  CP_TRY(d2h(c->Epair, 2 * c->es * (c->N + 1)));
   CP_TRY(d2h(c->phi, sizeof(double) * (c->N + 1)));
   CP_TRY(d2h(c->E64, sizeof(double) * c->N));
   CP_TRY(d2h(c->Glast, sizeof(long long) * (c->N + 1)));
@@ -666,7 +704,7 @@ int cp_load_state(cp_ctx* c, const void* buf, size_t len) {
     CP_TRY(h2d(S.u[s], c->es * h.slots[s]));
   }
   CP_TRY(h2d(S.id, 4 * h.slots[1]));
-  CP_TRY(h2d(c->Epad, c->es * (c->N + 2)));
+  CP_TRY(h2d(c->Epair, 2 * c->es * (c->N + 1)));
   CP_TRY(h2d(c->phi, sizeof(double) * (c->N + 1)));
   CP_TRY(h2d(c->E64, sizeof(double) * c->N));
   CP_TRY(h2d(c->Glast, sizeof(long long) * (c->N + 1)));
@@ -681,14 +719,16 @@ int cp_load_state(cp_ctx* c, const void* buf, size_t len) {
 int cp_enable_timing(cp_ctx* c, int32_t on) {
   if (!c) return CP_ERR_ARG;
   c->timing = (on != 0);
-  c->t_ms[0] = c->t_ms[1] = 0.0;
-  c->t_n[0] = c->t_n[1] = 0;
+  for (int k = 0; k < 3; ++k) {
+    c->t_ms[k] = 0.0;
+    c->t_n[k] = 0;
+  }
   return CP_OK;
 }
 
-int cp_read_timing(cp_ctx* c, double ms[2], int64_t n[2]) {
+int cp_read_timing(cp_ctx* c, double ms[3], int64_t n[3]) {
   if (!c || !ms || !n) return CP_ERR_ARG;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     ms[k] = c->t_ms[k];
     n[k] = c->t_n[k];
   }

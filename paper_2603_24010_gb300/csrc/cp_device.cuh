@@ -9,12 +9,15 @@
 //   particles; the live buffer pointers live in DevState so that captured
 //   CUDA graphs stay valid across swaps.
 //   G[N+1]        int64 charge grid being deposited for the next level
+//                 (2^16 units per macroparticle charge)
 //   Glast[N+1]    int64 charge grid of the current level (read-back copy)
-//   Epad[N+2]     half-grid field of the current level in particle precision,
-//                 padded with a copy of each end value (index k+1 = E_{k+1/2})
+//   Epair[N+1]    gather table of the current level in particle precision:
+//                 pair k = (Ep_k, Ep_{k+1} - Ep_k) with Ep_0 = E_{1/2},
+//                 Ep_k = E_{k-1/2} (k = 1..N), Ep_{N+1} = E_{N-1/2}
 //   phi[N+1], E64[N]  FP64 potential and field of the current level
 //   abs[grid*cap] per-CTA lists of ions absorbed in the current push
 //   hist[rows]    one cp_diag row per level
+//   vs[rows]      source voltage polarity V_s(t_n) per level
 //
 // A dead (absorbed) particle has xi <= 0; live particles have 0 < xi < N.
 #pragma once
@@ -26,9 +29,14 @@
 namespace cpk {
 
 constexpr int kSpecies = 3;
-constexpr int kThreads = 512;          // threads per CTA of the step kernel
-constexpr int kCtasPerSm = 2;          // resident CTAs per SM
+constexpr int kThreads = 512;          // threads per CTA of the push kernel
+constexpr int kCtasPerSm = 2;          // resident push CTAs per SM
 constexpr int kPerThread = 4;          // particles per thread per tile (one 16 B vector for FP32)
+constexpr int kTile = kThreads * kPerThread;  // particles per CTA tile
+constexpr int kFlushTiles = 31;        // tiles between flushes of the 32-bit cell sums
+constexpr int kSolveCtas = 8;          // CTAs (one cluster) of the coupled solve
+constexpr int kSolveThreads = 512;
+constexpr double kFix = 65536.0;       // fixed-point units per macroparticle charge
 constexpr uint64_t kTagSee = 0x5345ULL;
 constexpr uint64_t kTagBeam = 0x4245ULL;
 
@@ -45,6 +53,18 @@ struct DevParams {
   double scale;          // rho_i = G_i * scale  [C/m^3]
   double kappa[kSpecies];  // q dt^2 / (m dx): cells/step^2 per V/m
   double see_vth;        // sqrt(e T_emit / m_e)
+  double a21;            // 9 L / (4 dt^2) + 3 R / (2 dt): BDF2 coefficient of Q^n
+  double alpha;          // dx^2 * scale / eps0: b_i = -alpha G_i
+  // host-precomputed factors so that the solve divides nothing in FP64
+  double g_strict;       // 1 / a21
+  double g_weak;         // 1 / (a21 + 1/C)
+  double gam_strict;     // g_strict dx / (eps0 A)
+  double inv_den_strict; // 1 / (1 + N gam_strict)
+  double dx_eps0;        // dx / eps0
+  double inv_A, inv_dx, inv_2dt;
+  double L4dt2, R2dt;    // L / (4 dt^2), R / (2 dt)
+  float kap_f[2][kSpecies];   // kick factors in FP32: [0] half kick, [1] full kick
+  double kap_d[2][kSpecies];  // the same in FP64
   int64_t cap[kSpecies];
   int32_t abs_cap;       // absorbed-ion records per CTA
   int32_t precision;
@@ -79,7 +99,6 @@ struct DevState {
   long long conv_count;
   long long ion_energy_q;     // sum of rint(256 E_eV) over ions absorbed at x = 0
   unsigned int max_cfl_bits;  // float bits of max |u| (non-negative floats order as ints)
-  unsigned int done_ctas;     // arrival ticket for the last-CTA solve
   unsigned long long compact_n[kSpecies];
   unsigned int compact_done;
   uint32_t beam_id_base;
@@ -91,12 +110,13 @@ struct Bufs {
   DevState* S;
   long long* G;
   long long* Glast;
-  void* Epad;
+  void* Epair;
   double* phi;
   double* E64;
   AbsRec* abs;
   cp_diag* hist;
   int64_t hist_rows;
+  const double* vs;  // polarity V_s(t_n) for every level n (filled once at set-up)
 };
 
 // ---------------------------------------------------------------------------

@@ -1,30 +1,52 @@
-// cp_kernels.cu -- the fused PIC step kernel and the coupled field solve.
+// cp_kernels.cu -- the PIC step kernels: particle push and coupled solve.
 //
-// One launch of k_step advances one time level (arXiv 2603.24010):
-//   1. every CTA stages the half-grid field E^n (Epad) in shared memory and
-//      streams its share of the particle store with 16-byte vector loads:
-//      CIC gather (App. C), leapfrog kick and drift (Sec. 2.2.2), absorption
-//      test at both electrodes (Sec. 2.4.1) and int64 fixed-point CIC
-//      deposit into a shared-memory grid with the boundary-node doubling of
-//      App. E.2;
-//   2. each CTA then turns the ions it saw absorbed into secondary electrons
-//      (Sec. 2.3, Algorithm see_sampling_1d; Philox4x64-10 draws keyed by
-//      (seed, step, ion id)), appends them with warp-aggregated atomics and
-//      deposits them; the CTAs also inject the beam ions of this step;
-//   3. the shared-memory grids are added into the global int64 grid and the
-//      per-CTA tallies into the device state;
-//   4. the last CTA to finish (arrival ticket, no spinning) solves the
-//      coupled Poisson/circuit system of the new level in FP64 and writes
-//      E^{n+1} for the next launch (Sec. 2.4.2 strict, Sec. 2.4.3 weak).
+// One time step (arXiv 2603.24010) is two launches:
+//
+// k_push  (persistent grid, 2 CTAs per SM) streams every particle once with
+//   16-byte vector loads/stores: CIC gather of E^n from a shared-memory
+//   table (App. C), leapfrog kick and drift (Sec. 2.2.2), absorption at the
+//   electrodes (Sec. 2.4.1), and the CIC deposit of rho^{n+1} in fixed point
+//   (2^16 units per macroparticle charge, boundary nodes doubled as in
+//   App. E.2) into per-cell 32-bit shared-memory sums that are folded into a
+//   shared int64 node grid every 31 tiles (so no 32-bit sum can overflow).
+//   Each CTA then turns the ions it saw absorbed into secondary electrons
+//   (Sec. 2.3, Algorithm see_sampling_1d; Philox4x64-10 draws keyed by
+//   (seed, step, ion id)), appends them with warp-aggregated atomics and
+//   deposits them; the CTAs share the injection of the step's beam ions.
+//   The int64 node grids and the tallies are added into global memory.
+//
+// k_solve (one thread-block cluster of 8 CTAs x 512 threads) solves the new
+//   level: the bordered tridiagonal system of App. B with the circuit row of
+//   Sec. 2.4.2 (strict, Eq. Poisson_BC2) or Sec. 2.4.3 (weak, Eq.
+//   Poisson_BC3) is factorised into two bidiagonal scans whose charge sums
+//   are exact integers (int64 prefix of the charge grid, int128 prefix of
+//   that); FP64 enters only at the final scaling, so the solve is direct and
+//   its backward error is checked over every row and the circuit row, with
+//   FP64 iterative refinement if it exceeds the requested tolerance.  Chunk
+//   totals are exchanged through distributed shared memory.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "cp_device.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace cpk {
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename real>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
 
 // ---------------------------------------------------------------------------
 // 16-byte vector access to 4 consecutive particles (streaming cache hints:
@@ -47,42 +69,52 @@ __device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
   __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
 }
 
-__device__ __forceinline__ unsigned int frac_to_u32(float f) {
-  return __float2uint_rz(f * 4294967296.0f);  // exact: power-of-two scaling of f < 1
-}
-__device__ __forceinline__ unsigned int frac_to_u32(double f) {
-  return __double2uint_rz(f * 4294967296.0);
-}
+// floor(f 2^16) of a fraction f in [0, 1): exact power-of-two scaling, truncation
+__device__ __forceinline__ unsigned int frac_to_fix(float f) { return __float2uint_rz(f * 65536.0f); }
+__device__ __forceinline__ unsigned int frac_to_fix(double f) { return __double2uint_rz(f * 65536.0); }
 
-// Linear interpolation of the padded half-grid field at xi in (0, N):
-// Es[j+1] = E_{j+1/2}, with Es[0] = E_{1/2} and Es[N+1] = E_{N-1/2} so that
-// the field is constant between a wall and the first half-grid point.
+// Linear interpolation between half-grid points from the pair table:
+// pair j+1 = (E_{j+1/2}, E_{j+3/2} - E_{j+1/2}) with constant ends.
 template <typename real>
-__device__ __forceinline__ real gather(const real* Es, real x) {
+__device__ __forceinline__ real gather(const typename Pair<real>::type* Es2, real x) {
   const real s = x - real(0.5);
   const real jf = floor(s);
   const int j = static_cast<int>(jf);
   const real t = s - jf;
-  const real e0 = Es[j + 1];
-  const real e1 = Es[j + 2];
-  return fma(t, e1 - e0, e0);
+  const typename Pair<real>::type e = Es2[j + 1];
+  return fma(t, e.y, e.x);
 }
 
-// CIC deposit in fixed point: W1 = floor(f 2^32) on node i+1, 2^32 - W1 on
-// node i, boundary nodes doubled.
+// CIC deposit into the per-cell 32-bit sums: A[i] += 2^16 - W1 (node i),
+// Bc[i] += W1 (node i+1).  Native 32-bit shared atomics.
 template <typename real>
-__device__ __forceinline__ void deposit(long long* Gs, int N, real x, long long sign) {
+__device__ __forceinline__ void deposit(unsigned int* A, unsigned int* Bc, real x) {
   const real fl = floor(x);
   const int i = static_cast<int>(fl);
-  const long long w1 = static_cast<long long>(frac_to_u32(x - fl));
-  long long w0 = (1LL << 32) - w1;
-  long long w1b = w1;
-  if (i == 0) w0 <<= 1;
-  if (i == N - 1) w1b <<= 1;
-  atomicAdd(reinterpret_cast<unsigned long long*>(&Gs[i]),
-            static_cast<unsigned long long>(sign * w0));
-  atomicAdd(reinterpret_cast<unsigned long long*>(&Gs[i + 1]),
-            static_cast<unsigned long long>(sign * w1b));
+  const unsigned int w1 = frac_to_fix(x - fl);
+  atomicAdd(&A[i], 65536u - w1);
+  atomicAdd(&Bc[i], w1);
+}
+
+// Fold the cell sums into the int64 node grid (node k gets A[k] + Bc[k-1],
+// the two end nodes doubled) and clear them.  Thread k owns node k and is
+// the only reader of A[k] and Bc[k-1], so it clears exactly those.
+__device__ __forceinline__ void fold(unsigned int* A, unsigned int* Bc, long long* Gs, int N,
+                                     long long sign) {
+  for (int k = threadIdx.x; k <= N; k += kThreads) {
+    long long a = 0, b = 0;
+    if (k < N) {
+      a = A[k];
+      A[k] = 0u;
+    }
+    if (k > 0) {
+      b = Bc[k - 1];
+      Bc[k - 1] = 0u;
+    }
+    if (k == 0) a <<= 1;
+    if (k == N) b <<= 1;
+    if (a | b) Gs[k] += sign * (a + b);
+  }
 }
 
 template <typename real>
@@ -131,138 +163,9 @@ __device__ __forceinline__ unsigned int warp_max_u(unsigned int v) {
   return v;
 }
 
-// ---------------------------------------------------------------------------
-// Block-wide scans and reductions in FP64 (one CTA, kThreads threads)
-// ---------------------------------------------------------------------------
-__device__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane_id() == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = (threadIdx.x < kThreads / 32) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[0] = t;
-  }
-  __syncthreads();
-  t = red[0];
-  __syncthreads();
-  return t;
-}
-
-__device__ double block_max(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane_id() == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = (threadIdx.x < kThreads / 32) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (threadIdx.x == 0) red[0] = t;
-  }
-  __syncthreads();
-  t = red[0];
-  __syncthreads();
-  return t;
-}
-
-// In-place inclusive scan of a[idx(m)], m = 0..n-1, where idx(m) = m or
-// n-1-m (reverse = suffix sums).  Each thread owns a contiguous run of m.
-__device__ void block_incl_scan(double* a, int n, bool reverse, double* red) {
-  const int per = (n + kThreads - 1) / kThreads;
-  const int lo = min(static_cast<int>(threadIdx.x) * per, n);
-  const int hi = min(lo + per, n);
-  double s = 0.0;
-  for (int m = lo; m < hi; ++m) s += a[reverse ? n - 1 - m : m];
-  double incl = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (static_cast<int>(lane_id()) >= o) incl += y;
-  }
-  const int w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane_id() == 31) red[w] = incl;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = (threadIdx.x < kThreads / 32) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_up_sync(0xffffffffu, t, o);
-      if (static_cast<int>(threadIdx.x) >= o) t += y;
-    }
-    red[threadIdx.x] = t;
-  }
-  __syncthreads();
-  double run = (w > 0 ? red[w - 1] : 0.0) + (incl - s);
-  for (int m = lo; m < hi; ++m) {
-    const int k = reverse ? n - 1 - m : m;
-    run += a[k];
-    a[k] = run;
-  }
-  __syncthreads();
-}
-
-// Direct solve of the N x N system with rows
-//   (1 + gam) x_0 - x_1 = b_0,   x_{i-1} - 2 x_i + x_{i+1} = b_i (i >= 1), x_N = 0,
-// the x = 0 Gauss row and the finite-difference Laplacian of App. B.  The
-// matrix factors into two bidiagonals: with D_i = x_i - x_{i+1},
-//   D_i = D_0 - sum_{j=1..i} b_j,  D_0 = b_0 - gam x_0,  x_i = sum_{k>=i} D_k,
-// so x_0 (1 + N gam) = N b_0 - sum_i sum_{j=1..i} b_j.  In place: on entry
-// a[i] = b_i (a[0] ignored, b_0 passed), on exit a[i] = x_i for i < N.
-__device__ void tri_solve_inplace(double* a, int N, double b0, double gam, double* red,
-                                  double* s_scalar) {
-  if (threadIdx.x == 0) a[0] = 0.0;
-  __syncthreads();
-  block_incl_scan(a, N, false, red);  // a[i] = B_i = sum_{j=1..i} b_j
-  double part = 0.0;
-  for (int i = threadIdx.x; i < N; i += kThreads) part += a[i];
-  const double T = block_sum(part, red);
-  if (threadIdx.x == 0) {
-    const double x0 = (static_cast<double>(N) * b0 - T) / (1.0 + static_cast<double>(N) * gam);
-    s_scalar[0] = b0 - gam * x0;  // D_0
-  }
-  __syncthreads();
-  const double D0 = s_scalar[0];
-  for (int i = threadIdx.x; i < N; i += kThreads) a[i] = D0 - a[i];  // D_i
-  __syncthreads();
-  block_incl_scan(a, N, true, red);  // suffix sums: x_i
-}
-
-// Residual of the same system; returns the normwise backward error
-// max|r| / (||A|| max|x| + max|b|) and leaves r in `r`.
-__device__ double tri_residual(const double* x, const double* b, double b0, double gam, int N,
-                               double* r, double* red) {
-  double rm = 0.0, xm = 0.0, bm = 0.0;
-  for (int i = threadIdx.x; i < N; i += kThreads) {
-    const double xp = (i + 1 < N) ? x[i + 1] : 0.0;
-    double ri, bi;
-    if (i == 0) {
-      bi = b0;
-      ri = (1.0 + gam) * x[0] - xp - bi;
-    } else {
-      bi = b[i];
-      ri = x[i - 1] - 2.0 * x[i] + xp - bi;
-    }
-    r[i] = ri;
-    rm = fmax(rm, fabs(ri));
-    xm = fmax(xm, fabs(x[i]));
-    bm = fmax(bm, fabs(bi));
-  }
-  rm = block_max(rm, red);
-  xm = block_max(xm, red);
-  bm = block_max(bm, red);
-  const double nA = fmax(fabs(1.0 + gam) + 1.0, 4.0);
-  const double den = nA * xm + bm;
-  return den > 0.0 ? rm / den : 0.0;
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
 }
 
 __device__ __forceinline__ double source_voltage(const DevParams* P, double t) {
@@ -270,203 +173,12 @@ __device__ __forceinline__ double source_voltage(const DevParams* P, double t) {
   return P->V0 * (1.0 - cos(2.0 * pi * P->f * t)) * exp(-t / P->tau) / 2.0;
 }
 
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) {
-  return __ldcg(p);
-}
-
 // ---------------------------------------------------------------------------
-// Coupled solve of the new level by the last CTA (Sec. 2.4.2 / 2.4.3).
+// k_push
 // ---------------------------------------------------------------------------
 template <typename real>
-__device__ void solve_commit(const Bufs& B, int do_push, int mode, double tol,
-                             unsigned char* smem) {
-  const DevParams* P = B.P;
-  DevState* S = B.S;
-  const int N = P->N;
-  double* b = reinterpret_cast<double*>(smem);  // N
-  double* x = b + N;                            // N + 1
-  double* w = x + (N + 1);                      // N + 1
-  __shared__ double red[32];
-  __shared__ double sc[24];
-
-  const int64_t level = ldcg(&S->level) + (do_push ? 1 : 0);
-  const double dt = P->dt, dx = P->dx, A = P->area, eps0 = P->eps0;
-  const double qw = P->e * P->weight;
-  const long long conv = do_push ? ldcg(&S->conv_count) : 0LL;
-
-  // RHS of the Poisson rows 1..N-1 (Eq. dt_Poisson_app) and the grids
-  for (int i = threadIdx.x; i <= N; i += kThreads) {
-    const long long g = ldcg(&B.G[i]);
-    B.Glast[i] = g;
-    B.G[i] = 0;
-    if (i < N) b[i] = -dx * dx * (static_cast<double>(g) * P->scale) / eps0;
-  }
-  if (threadIdx.x == 0) {
-    const double t = static_cast<double>(level) * dt;
-    const double Vs = P->polarity * source_voltage(P, t);
-    const double Q1 = ldcg(&S->Qh[0]), Q2 = ldcg(&S->Qh[1]);
-    const double Q3 = ldcg(&S->Qh[2]), Q4 = ldcg(&S->Qh[3]);
-    const double a2 = 9.0 * P->L / (4.0 * dt * dt);
-    const double a1 = 3.0 * P->R / (2.0 * dt);
-    const double hist = P->L * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) / (4.0 * dt * dt) +
-                        P->R * (4.0 * Q1 - Q2) / (2.0 * dt);
-    double g = 0.0, Qpart = Q1, gam = 0.0;
-    if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
-      if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
-        g = 1.0 / (a2 + a1);
-        Qpart = g * (Vs + hist);
-        gam = g * dx / (eps0 * A);
-      } else {  // weak: free circuit with its load capacitor gives Q*^n
-        Qpart = (Vs + hist) / (a2 + a1 + 1.0 / P->C);
-      }
-    }
-    const double Qconv = static_cast<double>(conv) * qw;
-    const double sigma_prev = ldcg(&S->sigma);
-    const double rho0 = static_cast<double>(ldcg(&B.Glast[0])) * P->scale;
-    // x = 0 row: Eq. Poisson_BC2 (strict) or Eq. Poisson_BC3 (weak)
-    const double b0 = (dx * dx / eps0) * ((sigma_prev + (Qconv + Qpart - Q1) / A) / dx + rho0 / 2.0);
-    sc[0] = b0; sc[1] = gam; sc[2] = g; sc[3] = Qpart; sc[4] = Vs; sc[5] = hist;
-    sc[6] = a2 + a1; sc[7] = Qconv; sc[8] = sigma_prev; sc[9] = Q1; sc[10] = Q2; sc[11] = t;
-    sc[12] = Q3;
-  }
-  __syncthreads();
-  const double b0 = sc[0], gam = sc[1];
-  for (int i = threadIdx.x; i < N; i += kThreads) w[i] = b[i];
-  __syncthreads();
-  tri_solve_inplace(w, N, b0, gam, red, sc + 16);
-  for (int i = threadIdx.x; i < N; i += kThreads) x[i] = w[i];
-  if (threadIdx.x == 0) x[N] = 0.0;
-  __syncthreads();
-
-  // Backward error of the Poisson rows and of the circuit row; refine.
-  const bool strict_rlc = (P->circuit == CP_CIRCUIT_SERIES_RLC && mode == 0);
-  double eta = 0.0;
-  for (int sweep = 0; sweep <= 3; ++sweep) {
-    eta = tri_residual(x, b, b0, gam, N, w, red);
-    if (strict_rlc) {
-      const double Qn = sc[3] - sc[2] * x[0];
-      const double kvl = sc[6] * Qn - (sc[4] + sc[5]) + x[0];
-      const double kden = sc[6] * fabs(Qn) + fabs(sc[4] + sc[5]) + fabs(x[0]);
-      if (kden > 0.0) eta = fmax(eta, fabs(kvl) / kden);
-    }
-    if (!(eta > tol) || sweep == 3) break;
-    const double r0 = w[0];
-    __syncthreads();
-    tri_solve_inplace(w, N, r0, gam, red, sc + 16);
-    for (int i = threadIdx.x; i < N; i += kThreads) x[i] -= w[i];
-    __syncthreads();
-  }
-
-  // Field of the new level, padded copy in particle precision.
-  real* Epad = reinterpret_cast<real*>(B.Epad);
-  for (int i = threadIdx.x; i < N; i += kThreads) {
-    const double xp = (i + 1 < N) ? x[i + 1] : 0.0;
-    const double E = (x[i] - xp) / dx;  // Eq. dt_E-field
-    B.E64[i] = E;
-    Epad[i + 1] = static_cast<real>(E);
-    if (i == 0) Epad[0] = static_cast<real>(E);
-    if (i == N - 1) Epad[N + 1] = static_cast<real>(E);
-  }
-  for (int i = threadIdx.x; i <= N; i += kThreads) B.phi[i] = x[i];
-  __syncthreads();
-
-  if (threadIdx.x == 0) {
-    const double phi0 = x[0];
-    const double Qconv = sc[7], sigma_prev = sc[8], Q1 = sc[9], Q2 = sc[10];
-    double Qn, sigma_n, I;
-    if (strict_rlc) {
-      Qn = sc[3] - sc[2] * phi0;
-      sigma_n = sigma_prev + (Qconv + Qn - Q1) / A;  // Eq. sigma_update
-      I = (3.0 * Qn - 4.0 * Q1 + Q2) / (2.0 * dt);
-    } else if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
-      sigma_n = sigma_prev + (Qconv + sc[3] - Q1) / A;  // Eq. top_plate_charge with Q*^n
-      Qn = P->C * phi0;                                 // weak overwrite Q^n := C phi_0^n
-      I = (3.0 * sc[3] - 4.0 * Q1 + Q2) / (2.0 * dt);
-    } else {
-      sigma_n = sigma_prev + Qconv / A;
-      Qn = Q1;
-      I = 0.0;
-    }
-    int status = 0;
-    if (!isfinite(phi0) || !isfinite(sigma_n) || !isfinite(Qn)) status = CP_ERR_NONFINITE;
-    else if (eta > tol) status = CP_ERR_RESIDUAL;
-
-    cp_diag d;
-    d.step = level;
-    d.t = sc[11];
-    d.V_gap = phi0;
-    d.I_circ = I;
-    d.Q_surf = sigma_n * A;
-    d.Q_conv = Qconv;
-    d.Q_circ = Qn;
-    d.V_source = sc[4];
-    d.residual = eta;
-    d.ion_energy_eV = do_push ? static_cast<double>(ldcg(&S->ion_energy_q)) / 256.0 : 0.0;
-    d.max_cfl = do_push ? static_cast<double>(__uint_as_float(ldcg(&S->max_cfl_bits))) : 0.0;
-    d.pad = 0.0;
-    long long nl[kSpecies];
-    for (int s = 0; s < kSpecies; ++s) {
-      for (int e = 0; e < 2; ++e) {
-        const unsigned long long a = do_push ? ldcg(&S->absorbed[e][s]) : 0ULL;
-        d.absorbed[e][s] = static_cast<int64_t>(a);
-      }
-      nl[s] = ldcg(&S->n_live[s]) - d.absorbed[0][s] - d.absorbed[1][s];
-    }
-    d.emitted[0] = do_push ? static_cast<int64_t>(ldcg(&S->emitted[0])) : 0;
-    d.emitted[1] = do_push ? static_cast<int64_t>(ldcg(&S->emitted[1])) : 0;
-    d.injected = do_push ? static_cast<int64_t>(ldcg(&S->injected)) : 0;
-    nl[1] += d.injected;
-    nl[2] += d.emitted[0] + d.emitted[1];
-    for (int s = 0; s < kSpecies; ++s) d.n_live[s] = nl[s];
-    d.conv_count = conv;
-    S->cur = d;
-    if (level < B.hist_rows) B.hist[level] = d;
-
-    // commit the circuit and surface-charge state of the new level
-    S->sigma = sigma_n;
-    S->Qh[3] = sc[12];
-    S->Qh[2] = Q2;
-    S->Qh[1] = Q1;
-    S->Qh[0] = Qn;
-    S->level = level;
-    if (do_push) S->pushed = 1;
-    for (int s = 0; s < kSpecies; ++s) {
-      S->n_live[s] = nl[s];
-      for (int e = 0; e < 2; ++e) S->absorbed[e][s] = 0ULL;
-    }
-    S->emitted[0] = S->emitted[1] = 0ULL;
-    S->injected = 0ULL;
-    S->conv_count = 0;
-    S->ion_energy_q = 0;
-    S->max_cfl_bits = 0u;
-    S->done_ctas = 0u;
-    if (status != 0 && ldcg(&S->status) == 0) S->status = status;
-  }
-  // next push processes the slots in use, rounded up to whole vectors; the
-  // padding slots are made dead here
-  if (threadIdx.x < kSpecies) {
-    const int s = threadIdx.x;
-    long long na = static_cast<long long>(ldcg(&S->n_alloc[s]));
-    if (na > P->cap[s]) na = P->cap[s];
-    const long long na4 = (na + 3) & ~3LL;
-    real* xs = reinterpret_cast<real*>(S->xi[s]);
-    real* us = reinterpret_cast<real*>(S->u[s]);
-    for (long long k = na; k < na4; ++k) {
-      xs[k] = real(-1);
-      us[k] = real(0);
-    }
-    S->n_alloc[s] = na4;
-    S->n_proc[s] = na4;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The step kernel.
-// ---------------------------------------------------------------------------
-template <typename real>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
-    k_step(Bufs B, int do_push, int mode, double tol) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push(Bufs B, int do_push) {
+  using real2 = typename Pair<real>::type;
   const DevParams* __restrict__ P = B.P;
   DevState* S = B.S;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -475,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
   __shared__ unsigned long long s_cnt[2][kSpecies];
   __shared__ unsigned long long s_emit[2];
   __shared__ long long s_conv, s_energy;
-  __shared__ unsigned int s_cfl, s_ticket;
+  __shared__ unsigned int s_cfl;
 
   if (threadIdx.x == 0) {
     s_flag[0] = (ldcg(&S->status) != 0);
@@ -491,14 +203,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
   if (s_flag[0]) return;
 
   const int N = P->N;
+  const int64_t step = S->level;
+
   long long* Gs = reinterpret_cast<long long*>(smem);
-  real* Es = reinterpret_cast<real*>(smem + align16(sizeof(long long) * (N + 1)));
-  const real* Epad = reinterpret_cast<const real*>(B.Epad);
-  for (int k = threadIdx.x; k < N + 2; k += kThreads) Es[k] = Epad[k];
-  for (int k = threadIdx.x; k <= N; k += kThreads) Gs[k] = 0;
+  unsigned int* A = reinterpret_cast<unsigned int*>(smem + align16(sizeof(long long) * (N + 1)));
+  unsigned int* Bc = A + N;
+  real2* Es2 = reinterpret_cast<real2*>(smem + align16(sizeof(long long) * (N + 1)) +
+                                        align16(sizeof(unsigned int) * 2 * N));
+  const real2* Epair = reinterpret_cast<const real2*>(B.Epair);
+  for (int k = threadIdx.x; k <= N; k += kThreads) {
+    Es2[k] = Epair[k];
+    Gs[k] = 0;
+  }
+  for (int k = threadIdx.x; k < 2 * N; k += kThreads) A[k] = 0u;
   __syncthreads();
 
-  const int64_t step = S->level;
   const bool half = (S->pushed == 0);
   const real Nr = static_cast<real>(N);
   const int cap = P->abs_cap;
@@ -508,64 +227,93 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
   for (int s = 0; s < kSpecies; ++s) {
     real* __restrict__ xs = reinterpret_cast<real*>(S->xi[s]);
     real* __restrict__ us = reinterpret_cast<real*>(S->u[s]);
-    const int64_t n = S->n_proc[s];
+    const int64_t n = S->n_proc[s];  // multiple of 4
+    const int64_t ntiles = (n + kTile - 1) / kTile;
     const long long sign = (s == CP_IONS) ? 1LL : -1LL;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads * kPerThread;
-    int64_t base = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) * kPerThread;
-    if (do_push) {
-      const real kap = static_cast<real>(half ? 0.5 * P->kappa[s] : P->kappa[s]);
-      const uint32_t* ids = S->id;
-      unsigned int a0 = 0u, a1 = 0u;
-      for (; base < n; base += stride) {
-        real xv[4], uv[4];
-        load4(xs + base, xv);
-        load4(us + base, uv);
+    real kap;
+    if constexpr (sizeof(real) == 4) kap = P->kap_f[half ? 0 : 1][s];
+    else kap = P->kap_d[half ? 0 : 1][s];
+    const uint32_t* ids = S->id;
+    unsigned int a0 = 0u, a1 = 0u;
+    int since = 0;
+    // two tiles in flight per thread: the next tile's loads are issued
+    // before the current tile is processed
+    real xv[4], uv[4];
+    int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + static_cast<int64_t>(threadIdx.x) * kPerThread;
+    if (base < n) {
+      load4(xs + base, xv);
+      if (do_push) load4(us + base, uv);
+    }
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int64_t bnext = base + static_cast<int64_t>(gridDim.x) * kTile;
+      real xq[4], uq[4];
+      const bool more = bnext < n;
+      if (more) {
+        load4(xs + bnext, xq);
+        if (do_push) load4(us + bnext, uq);
+      }
+      if (base < n) {
+        if (do_push) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (xv[q] > real(0) && xv[q] < Nr) {  // live (dead slots hold -1)
-            const real E = gather(Es, xv[q]);
-            const real un = fma(kap, E, uv[q]);
-            const real xn = xv[q] + un;
-            cfl = max(cfl, __float_as_uint(fabsf(static_cast<float>(un))));
-            if (!(xn > real(0) && xn < Nr)) {  // absorbed (a non-finite value counts at x = d)
-              const int el = (xn <= real(0)) ? 0 : 1;
-              if (el) ++a1; else ++a0;
-              if (s == CP_IONS) {
-                const int slot = atomicAdd(&s_abs_n, 1);
-                if (slot < cap) {
-                  AbsRec r;
-                  r.id = ids[base + q];
-                  r.electrode = static_cast<uint32_t>(el);
-                  r.u = static_cast<double>(un);
-                  my_abs[slot] = r;
+          for (int q = 0; q < 4; ++q) {
+            if (xv[q] > real(0) && xv[q] < Nr) {  // live (dead slots hold -1)
+              const real E = gather<real>(Es2, xv[q]);
+              const real un = fma(kap, E, uv[q]);
+              const real xn = xv[q] + un;
+              cfl = max(cfl, __float_as_uint(fabsf(static_cast<float>(un))));
+              if (!(xn > real(0) && xn < Nr)) {  // absorbed (a non-finite value counts at x = d)
+                const int el = (xn <= real(0)) ? 0 : 1;
+                if (el) ++a1; else ++a0;
+                if (s == CP_IONS) {
+                  const int slot = atomicAdd(&s_abs_n, 1);
+                  if (slot < cap) {
+                    AbsRec r;
+                    r.id = ids[base + q];
+                    r.electrode = static_cast<uint32_t>(el);
+                    r.u = static_cast<double>(un);
+                    my_abs[slot] = r;
+                  }
                 }
+                xv[q] = real(-1);
+                uv[q] = real(0);
+              } else {
+                deposit<real>(A, Bc, xn);
+                xv[q] = xn;
+                uv[q] = un;
               }
-              xv[q] = real(-1);
-              uv[q] = real(0);
-            } else {
-              deposit(Gs, N, xn, sign);
-              xv[q] = xn;
-              uv[q] = un;
             }
           }
-        }
-        store4(xs + base, xv);
-        store4(us + base, uv);
-      }
-      a0 = warp_sum_u(a0);
-      a1 = warp_sum_u(a1);
-      if (lane_id() == 0) {
-        if (a0) atomicAdd(&s_cnt[0][s], static_cast<unsigned long long>(a0));
-        if (a1) atomicAdd(&s_cnt[1][s], static_cast<unsigned long long>(a1));
-      }
-    } else {
-      for (; base < n; base += stride) {
-        real xv[4];
-        load4(xs + base, xv);
+          store4(xs + base, xv);
+          store4(us + base, uv);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (xv[q] > real(0) && xv[q] < Nr) deposit(Gs, N, xv[q], sign);
+          for (int q = 0; q < 4; ++q)
+            if (xv[q] > real(0) && xv[q] < Nr) deposit<real>(A, Bc, xv[q]);
+        }
       }
+      if (more) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          xv[q] = xq[q];
+          uv[q] = uq[q];
+        }
+      }
+      base = bnext;
+      if (++since == kFlushTiles) {  // bounds every 32-bit cell sum below 2^32
+        __syncthreads();
+        fold(A, Bc, Gs, N, sign);
+        __syncthreads();
+        since = 0;
+      }
+    }
+    __syncthreads();
+    fold(A, Bc, Gs, N, sign);
+    __syncthreads();
+    a0 = warp_sum_u(a0);
+    a1 = warp_sum_u(a1);
+    if (lane_id() == 0) {
+      if (a0) atomicAdd(&s_cnt[0][s], static_cast<unsigned long long>(a0));
+      if (a1) atomicAdd(&s_cnt[1][s], static_cast<unsigned long long>(a1));
     }
   }
   cfl = warp_max_u(cfl);
@@ -622,21 +370,27 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
           if (slot < static_cast<unsigned long long>(P->cap[CP_SECONDARIES])) {
             xs[slot] = xr;
             us[slot] = ur;
-            deposit(Gs, N, xr, -1LL);
+            deposit<real>(A, Bc, xr);
           } else {
             s_flag[1] = 1;
           }
         }
       }
     }
+    __syncthreads();
+    if (na > 0) {  // at most 4096 impacts x (floor(gamma_max) + 1) electrons: no 32-bit overflow
+      fold(A, Bc, Gs, N, -1LL);
+      __syncthreads();
+    }
 
     // --- beam ions entering at x = d during this step ----------------------
     const int Bn = P->beam_per_step;
-    if (Bn > 0) {
+    if (Bn > 0 && static_cast<int>(blockIdx.x) * kThreads < Bn) {
       real* xs = reinterpret_cast<real*>(S->xi[CP_IONS]);
       real* us = reinterpret_cast<real*>(S->u[CP_IONS]);
       uint32_t* ids = S->id;
       const uint32_t id0 = S->beam_id_base;
+      int since = 0;
       for (int k0 = blockIdx.x * kThreads; k0 < Bn; k0 += gridDim.x * kThreads) {
         const int k = k0 + threadIdx.x;
         const bool act = k < Bn;
@@ -662,12 +416,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             xs[slot] = xr;
             us[slot] = static_cast<real>(-ub);
             ids[slot] = id0 + static_cast<uint32_t>(step * Bn + k);
-            deposit(Gs, N, xr, 1LL);
+            deposit<real>(A, Bc, xr);
           } else {
             s_flag[1] = 1;
           }
         }
+        if (++since == 4 * kFlushTiles) {  // 512 ions per pass: bounded cell sums
+          __syncthreads();
+          fold(A, Bc, Gs, N, 1LL);
+          __syncthreads();
+          since = 0;
+        }
       }
+      __syncthreads();
+      fold(A, Bc, Gs, N, 1LL);
     }
   }
   __syncthreads();
@@ -697,15 +459,550 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
       atomicAdd(&S->injected, static_cast<unsigned long long>(P->beam_per_step));
     if (s_flag[1]) atomicCAS(&S->status, 0, CP_ERR_CAPACITY);
   }
+}
 
-  // --- the last CTA to arrive solves the new level ---------------------------
-  __threadfence();
+// ---------------------------------------------------------------------------
+// Scans and reductions for the cluster solve
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long shfl_up_t(long long v, int o) {
+  return __shfl_up_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ double shfl_up_t(double v, int o) {
+  return __shfl_up_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ __int128 shfl_up_t(__int128 v, int o) {
+  const unsigned long long lo = static_cast<unsigned long long>(v);
+  const unsigned long long hi = static_cast<unsigned long long>(static_cast<unsigned __int128>(v) >> 64);
+  const unsigned long long l2 = __shfl_up_sync(0xffffffffu, lo, o);
+  const unsigned long long h2 = __shfl_up_sync(0xffffffffu, hi, o);
+  return static_cast<__int128>((static_cast<unsigned __int128>(h2) << 64) | l2);
+}
+
+// Sign-magnitude conversion: both 64-bit halves of |v| are non-negative, so
+// hi 2^64 + lo has no cancellation (error below 1 ulp of |v|).
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  const bool neg = v < 0;
+  const unsigned __int128 m = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
+  const unsigned long long hi = static_cast<unsigned long long>(m >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(m);
+  const double d = fma(static_cast<double>(hi), 18446744073709551616.0, static_cast<double>(lo));
+  return neg ? -d : d;
+}
+
+// In-place inclusive scan of a[idx(m)], m = 0..n-1 (idx = m, or n-1-m for a
+// suffix scan), contiguous runs per thread; returns the CTA total.
+template <typename T>
+__device__ T cta_scan(T* a, int n, bool reverse, T* wsum) {
+  const int per = (n + kSolveThreads - 1) / kSolveThreads;
+  const int lo = min(static_cast<int>(threadIdx.x) * per, n);
+  const int hi = min(lo + per, n);
+  T s = T(0);
+  for (int m = lo; m < hi; ++m) s += a[reverse ? n - 1 - m : m];
+  T incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = shfl_up_t(incl, o);
+    if (static_cast<int>(lane_id()) >= o) incl += y;
+  }
+  const int w = threadIdx.x >> 5;
   __syncthreads();
-  if (threadIdx.x == 0) s_ticket = atomicAdd(&S->done_ctas, 1u);
+  if (lane_id() == 31) wsum[w] = incl;
   __syncthreads();
-  if (s_ticket != gridDim.x - 1) return;
-  __threadfence();
-  solve_commit<real>(B, do_push, mode, tol, smem);
+  if (threadIdx.x < 32) {
+    T t = (threadIdx.x < kSolveThreads / 32) ? wsum[threadIdx.x] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = shfl_up_t(t, o);
+      if (static_cast<int>(threadIdx.x) >= o) t += y;
+    }
+    wsum[threadIdx.x] = t;
+  }
+  __syncthreads();
+  T run = (w > 0 ? wsum[w - 1] : T(0)) + (incl - s);
+  for (int m = lo; m < hi; ++m) {
+    const int k = reverse ? n - 1 - m : m;
+    run += a[k];
+    a[k] = run;
+  }
+  const T total = wsum[kSolveThreads / 32 - 1];
+  __syncthreads();
+  return total;
+}
+
+__device__ double cta_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane_id() == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < kSolveThreads / 32; ++k) t = fmax(t, red[k]);
+  __syncthreads();
+  return t;
+}
+
+__device__ double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane_id() == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < kSolveThreads / 32; ++k) t += red[k];
+  __syncthreads();
+  return t;
+}
+
+// Exclusive prefix (in rank order, or reverse rank order) and total over the
+// cluster of one value per CTA, through distributed shared memory.
+template <typename T>
+__device__ void cluster_prefix(T mine, T* slot, bool reverse, T* excl, T* total) {
+  cg::cluster_group cl = cg::this_cluster();
+  if (threadIdx.x == 0) *slot = mine;
+  cl.sync();
+  const unsigned me = cl.block_rank();
+  const unsigned nr = cl.num_blocks();
+  T acc = T(0), tot = T(0);
+  for (unsigned r = 0; r < nr; ++r) {
+    const T v = *cl.map_shared_rank(slot, r);
+    if (reverse ? (r > me) : (r < me)) acc += v;
+    tot += v;
+  }
+  *excl = acc;
+  *total = tot;
+  cl.sync();
+}
+
+__device__ double cluster_max(double mine, double* slot) {
+  cg::cluster_group cl = cg::this_cluster();
+  if (threadIdx.x == 0) *slot = mine;
+  cl.sync();
+  double m = 0.0;
+  for (unsigned r = 0; r < cl.num_blocks(); ++r) m = fmax(m, *cl.map_shared_rank(slot, r));
+  cl.sync();
+  return m;
+}
+
+// FP64 direct solve of the same tridiagonal system for an arbitrary right-hand
+// side (used by the refinement sweeps): on entry v[k] = b_{lo+k}, b0 = b_0;
+// on exit v[k] = x_{lo+k}.  D_i = D_0 - sum_{j=1..i} b_j, D_0 = b_0 - gam x_0,
+// x_0 (1 + N gam) = N b_0 - sum_i sum_{j=1..i} b_j, x_i = sum_{k>=i} D_k.
+__device__ void cluster_tri_solve_f64(double* v, int lo, int m, int N, double b0, double gam,
+                                      double* wsum, double* slot, double* sc) {
+  if (lo == 0 && threadIdx.x == 0 && m > 0) v[0] = 0.0;
+  __syncthreads();
+  double off, tot;
+  const double t1 = cta_scan(v, m, false, wsum);
+  cluster_prefix(t1, slot, false, &off, &tot);
+  double part = 0.0;
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) {
+    v[k] += off;  // B_i
+    part += v[k];
+  }
+  const double Tl = cta_sum(part, wsum);
+  double o2, T;
+  cluster_prefix(Tl, slot, false, &o2, &T);
+  if (threadIdx.x == 0) {
+    const double x0 = (static_cast<double>(N) * b0 - T) / (1.0 + static_cast<double>(N) * gam);
+    sc[0] = b0 - gam * x0;
+  }
+  __syncthreads();
+  const double D0 = sc[0];
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) v[k] = D0 - v[k];
+  __syncthreads();
+  const double t3 = cta_scan(v, m, true, wsum);  // suffix sums within the chunk
+  double o3, T3;
+  cluster_prefix(t3, slot, true, &o3, &T3);  // sums of the chunks after this one
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) v[k] += o3;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// k_solve: one cluster of kSolveCtas CTAs solves the new level.
+//
+// Rank r owns rows [lo, hi).  Four cluster barriers in the common case:
+//   A  per-rank totals of the two integer scans -> every rank's offsets
+//   B  chunk-edge potentials and fields (neighbour rows of the residual)
+//   C  per-rank maxima of |r|, |x|, |b| -> backward error
+//   D  keeps every rank's shared memory alive until all remote reads are done
+// ---------------------------------------------------------------------------
+struct SolveSlotA {
+  __int128 uloc;  // sum over the chunk of the chunk-local charge prefix
+  long long tg;   // sum over the chunk of G_i (i >= 1)
+  long long m;    // rows in the chunk
+};
+struct SolveSlotB {
+  double first_phi, last_phi, first_E, phi0;
+};
+struct SolveSlotC {
+  unsigned long long rmax, xmax, bmax;  // bit patterns of non-negative doubles
+};
+
+// |x| as the bit pattern of a non-negative double: such patterns order like
+// the values, so maxima can be taken on the integer pipe (GB300's FP64 pipe
+// is narrow).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+// Block maxima of three bit patterns; the result is valid in thread 0.
+__device__ void cta_max3(unsigned long long& a, unsigned long long& b, unsigned long long& c,
+                         unsigned long long (*red)[32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+  }
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane_id() == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+    red[2][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kSolveThreads / 32; ++k) {
+      a = max(a, red[0][k]);
+      b = max(b, red[1][k]);
+      c = max(c, red[2][k]);
+    }
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push, int mode, double tol) {
+  using real2 = typename Pair<real>::type;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int nr = static_cast<int>(cl.num_blocks());
+  const DevParams* P = B.P;
+  DevState* S = B.S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) __int128 w128[32];
+  __shared__ long long w64[32];
+  __shared__ double wd[3][32];
+  __shared__ unsigned long long wu[3][32];
+  __shared__ double s_eta;
+  __shared__ __align__(16) SolveSlotA slotA;
+  __shared__ SolveSlotB slotB;
+  __shared__ SolveSlotC slotC;
+  __shared__ double slotd;
+  __shared__ __align__(16) __int128 s_offP, s_U;
+  __shared__ long long s_offS;
+  __shared__ double sc[24];
+  __shared__ int s_stop;
+
+  if (threadIdx.x == 0) s_stop = (ldcg(&S->status) != 0);
+  __syncthreads();
+  if (s_stop) return;  // the status cannot change while this kernel runs: all ranks agree
+
+  const int N = P->N;
+  const int chunk = (N + nr - 1) / nr;
+  const int lo = min(rank * chunk, N);
+  const int hi = min(lo + chunk, N);
+  const int m = hi - lo;
+  long long* Sg = reinterpret_cast<long long*>(smem);                      // chunk
+  __int128* Pq = reinterpret_cast<__int128*>(smem + align16(8 * chunk));   // chunk
+  double* ph = reinterpret_cast<double*>(smem + align16(8 * chunk) + 16 * chunk);
+  double* Ee = ph + chunk;
+  double* bb = Ee + chunk;
+  double* rr = bb + chunk;
+
+  const long long G0 = ldcg(&B.G[0]);
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) {
+    const int i = lo + k;
+    const long long g = ldcg(&B.G[i]);
+    Sg[k] = (i == 0) ? 0LL : g;
+    B.Glast[i] = g;
+    if (i > 0) B.G[i] = 0;  // G_0 is cleared after every rank has read it
+  }
+  const bool last_rows = (hi == N && m > 0);  // this rank owns row N-1 (and node N)
+  if (last_rows && threadIdx.x == 0) {
+    B.Glast[N] = ldcg(&B.G[N]);
+    B.G[N] = 0;
+  }
+  // chunk-local exact prefixes: Sg = inclusive prefix of G_i (i >= 1),
+  // Pq = inclusive prefix of Sg
+  const long long tg = cta_scan(Sg, m, false, w64);
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) Pq[k] = static_cast<__int128>(Sg[k]);
+  __syncthreads();
+  const __int128 uloc = cta_scan(Pq, m, false, w128);
+
+  // --- barrier A: offsets of the global prefixes -----------------------------
+  if (threadIdx.x == 0) {
+    slotA.uloc = uloc;
+    slotA.tg = tg;
+    slotA.m = m;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    long long offS_r = 0, my_offS = 0;
+    __int128 acc = 0, my_offP = 0;
+    for (int r = 0; r < nr; ++r) {
+      const SolveSlotA* q = cl.map_shared_rank(&slotA, r);
+      if (r == rank) {
+        my_offS = offS_r;
+        my_offP = acc;
+      }
+      // sum over rank r's rows of S'_i = its local sum + m_r * (charge before it)
+      acc += q->uloc + static_cast<__int128>(q->m) * offS_r;
+      offS_r += q->tg;
+    }
+    s_offS = my_offS;
+    s_offP = my_offP;
+    s_U = acc;
+    if (rank == 0) B.G[0] = 0;
+  }
+  __syncthreads();
+  const long long offS = s_offS;
+  const __int128 offP = s_offP, U = s_U;
+
+  // circuit row (every rank evaluates the same scalars)
+  if (threadIdx.x == 0) {
+    const double dt = P->dt, dx = P->dx, A = P->area, eps0 = P->eps0;
+    const double qw = P->e * P->weight;
+    const long long conv = do_push ? ldcg(&S->conv_count) : 0LL;
+    const int64_t lev = ldcg(&S->level) + (do_push ? 1 : 0);
+    const double Vs = B.vs[lev];
+    const double Q1 = ldcg(&S->Qh[0]), Q2 = ldcg(&S->Qh[1]);
+    const double Q3 = ldcg(&S->Qh[2]), Q4 = ldcg(&S->Qh[3]);
+    const double hist = P->L4dt2 * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) + P->R2dt * (4.0 * Q1 - Q2);
+    double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
+    if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
+      if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
+        g = P->g_strict;
+        Qpart = g * (Vs + hist);
+        gam = P->gam_strict;
+        inv_den = P->inv_den_strict;
+      } else {  // weak: free circuit with its load capacitor gives Q*^n
+        Qpart = (Vs + hist) * P->g_weak;
+      }
+    }
+    const double Qconv = static_cast<double>(conv) * qw;
+    const double sigma_prev = ldcg(&S->sigma);
+    // x = 0 row: Eq. Poisson_BC2 (strict) / Eq. Poisson_BC3 (weak), with
+    // rho_0 dx^2 / (2 eps0) = alpha G_0 / 2 (G_0 is even: boundary doubling)
+    const double b0 = P->dx_eps0 * (sigma_prev + (Qconv + Qpart - Q1) * P->inv_A) +
+                      P->alpha * static_cast<double>(G0 / 2);
+    const double phi0 = (static_cast<double>(N) * b0 + P->alpha * i128_to_double(U)) * inv_den;
+    (void)dt; (void)dx; (void)A; (void)eps0;
+    sc[0] = b0; sc[1] = gam; sc[2] = g; sc[3] = Qpart; sc[4] = Vs; sc[5] = hist;
+    sc[6] = Qconv; sc[7] = sigma_prev; sc[8] = Q1; sc[9] = Q2; sc[10] = Q3;
+    sc[11] = b0 - gam * phi0;  // D_0 = x_0 - x_1
+    sc[12] = static_cast<double>(conv);
+  }
+  __syncthreads();
+  const double b0 = sc[0], gam = sc[1], D0 = sc[11];
+  const double alpha = P->alpha, inv_dx = P->inv_dx;
+  const double E0 = D0 * inv_dx, Ea = alpha * inv_dx;
+  // D_i = D_0 + alpha S'_i;  x_i = (N - i) D_0 + alpha (U - P_i);  E_i = D_i / dx
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) {
+    const int i = lo + k;
+    const long long Si = offS + Sg[k];
+    // exclusive global prefix of S' at row i
+    const __int128 Pi = offP + static_cast<__int128>(k) * offS + (Pq[k] - static_cast<__int128>(Sg[k]));
+    ph[k] = fma(static_cast<double>(N - i), D0, alpha * i128_to_double(U - Pi));
+    Ee[k] = fma(Ea, static_cast<double>(Si), E0);
+    const long long gi = (k == 0) ? Sg[0] : (Sg[k] - Sg[k - 1]);
+    bb[k] = (i == 0) ? b0 : -alpha * static_cast<double>(gi);
+  }
+  __syncthreads();
+
+  const bool strict_rlc = (P->circuit == CP_CIRCUIT_SERIES_RLC && mode == 0);
+  double eta = 0.0, nextE = 0.0;
+  for (int sweep = 0; sweep <= 3; ++sweep) {
+    // --- barrier B: edge values of the neighbouring chunks -------------------
+    if (threadIdx.x == 0 && m > 0) {
+      slotB.first_phi = ph[0];
+      slotB.last_phi = ph[m - 1];
+      slotB.first_E = Ee[0];
+      slotB.phi0 = ph[0];
+    }
+    cl.sync();
+    const double prev_phi = (rank > 0 && m > 0) ? cl.map_shared_rank(&slotB, rank - 1)->last_phi : 0.0;
+    const double next_phi = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_phi : 0.0;
+    nextE = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_E : 0.0;
+    const double phi0 = cl.map_shared_rank(&slotB, 0)->phi0;
+    unsigned long long rm = 0ULL, xm = 0ULL, bm = 0ULL;
+    for (int k = threadIdx.x; k < m; k += kSolveThreads) {
+      const int i = lo + k;
+      const double xp = (k + 1 < m) ? ph[k + 1] : next_phi;
+      double ri;
+      if (i == 0) {
+        ri = (1.0 + gam) * ph[k] - xp - bb[k];
+      } else {
+        const double xq = (k > 0) ? ph[k - 1] : prev_phi;
+        ri = xq - 2.0 * ph[k] + xp - bb[k];
+      }
+      rr[k] = ri;
+      rm = max(rm, abs_bits(ri));
+      xm = max(xm, abs_bits(ph[k]));
+      bm = max(bm, abs_bits(bb[k]));
+    }
+    cta_max3(rm, xm, bm, wu);
+    // --- barrier C: backward error over the cluster --------------------------
+    if (threadIdx.x == 0) {
+      slotC.rmax = rm;
+      slotC.xmax = xm;
+      slotC.bmax = bm;
+    }
+    cl.sync();
+    if (threadIdx.x == 0) {
+      for (int r = 0; r < nr; ++r) {
+        const SolveSlotC* q = cl.map_shared_rank(&slotC, r);
+        rm = max(rm, q->rmax);
+        xm = max(xm, q->xmax);
+        bm = max(bm, q->bmax);
+      }
+      const double rmd = __longlong_as_double(static_cast<long long>(rm));
+      const double xmd = __longlong_as_double(static_cast<long long>(xm));
+      const double bmd = __longlong_as_double(static_cast<long long>(bm));
+      const double nA = fmax(fabs(1.0 + gam) + 1.0, 4.0);
+      const double den = nA * xmd + bmd;
+      double e = den > 0.0 ? rmd / den : 0.0;
+      if (strict_rlc) {  // the circuit row with the potential of row 0
+        const double Qn = sc[3] - sc[2] * phi0;
+        const double kvl = P->a21 * Qn - (sc[4] + sc[5]) + phi0;
+        const double kden = P->a21 * fabs(Qn) + fabs(sc[4] + sc[5]) + fabs(phi0);
+        if (kden > 0.0) e = fmax(e, fabs(kvl) / kden);
+      }
+      s_eta = e;
+    }
+    __syncthreads();
+    eta = s_eta;
+    if (!(eta > tol) || sweep == 3) break;
+    // refinement: solve A delta = r, x -= delta (FP64; rare path)
+    const double r0 = (rank == 0) ? rr[0] : 0.0;
+    if (rank == 0 && threadIdx.x == 0) sc[14] = r0;
+    cl.sync();
+    const double r0all = cl.map_shared_rank(&sc[14], 0)[0];
+    cluster_tri_solve_f64(rr, lo, m, N, r0all, gam, wd[0], &slotd, sc + 16);
+    for (int k = threadIdx.x; k < m; k += kSolveThreads) ph[k] -= rr[k];
+    __syncthreads();
+    if (threadIdx.x == 0 && m > 0) slotB.first_phi = ph[0];
+    cl.sync();
+    const double np = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_phi : 0.0;
+    for (int k = threadIdx.x; k < m; k += kSolveThreads)
+      Ee[k] = (ph[k] - ((k + 1 < m) ? ph[k + 1] : np)) * inv_dx;
+    __syncthreads();
+  }
+
+  // outputs; the gather table pairs need the next chunk's first field value
+  real2* Epair = reinterpret_cast<real2*>(B.Epair);
+  for (int k = threadIdx.x; k < m; k += kSolveThreads) {
+    const int i = lo + k;
+    B.E64[i] = Ee[k];
+    B.phi[i] = ph[k];
+    const real e0 = static_cast<real>(Ee[k]);
+    const real e1 = (i + 1 < N) ? static_cast<real>((k + 1 < m) ? Ee[k + 1] : nextE) : e0;
+    real2 pr;
+    pr.x = e0;
+    pr.y = e1 - e0;
+    Epair[i + 1] = pr;
+    if (i == 0) {
+      real2 p0;
+      p0.x = e0;
+      p0.y = real(0);
+      Epair[0] = p0;
+    }
+  }
+  if (last_rows && threadIdx.x == 0) B.phi[N] = 0.0;
+  cl.sync();  // barrier D: keep every rank's shared memory alive until all remote reads are done
+  if (rank != 0) return;
+
+  if (threadIdx.x == 0) {
+    const int64_t level = S->level + (do_push ? 1 : 0);
+    const double dt = P->dt, A = P->area;
+    const double phi0 = ph[0];
+    const double Qconv = sc[6], sigma_prev = sc[7], Q1 = sc[8], Q2 = sc[9], Q3 = sc[10];
+    const long long conv = static_cast<long long>(sc[12]);
+    double Qn, sigma_n, I;
+    if (strict_rlc) {
+      Qn = sc[3] - sc[2] * phi0;
+      sigma_n = sigma_prev + (Qconv + Qn - Q1) * P->inv_A;  // Eq. sigma_update
+      I = (3.0 * Qn - 4.0 * Q1 + Q2) * P->inv_2dt;
+    } else if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
+      sigma_n = sigma_prev + (Qconv + sc[3] - Q1) * P->inv_A;  // Eq. top_plate_charge with Q*^n
+      Qn = P->C * phi0;                                        // weak overwrite Q^n := C phi_0^n
+      I = (3.0 * sc[3] - 4.0 * Q1 + Q2) * P->inv_2dt;
+    } else {
+      sigma_n = sigma_prev + Qconv * P->inv_A;
+      Qn = Q1;
+      I = 0.0;
+    }
+    int status = 0;
+    if (!isfinite(phi0) || !isfinite(sigma_n) || !isfinite(Qn)) status = CP_ERR_NONFINITE;
+    else if (eta > tol) status = CP_ERR_RESIDUAL;
+
+    cp_diag d;
+    d.step = level;
+    d.t = static_cast<double>(level) * dt;
+    d.V_gap = phi0;
+    d.I_circ = I;
+    d.Q_surf = sigma_n * A;
+    d.Q_conv = Qconv;
+    d.Q_circ = Qn;
+    d.V_source = sc[4];
+    (void)A;
+    d.residual = eta;
+    d.ion_energy_eV = do_push ? static_cast<double>(S->ion_energy_q) / 256.0 : 0.0;
+    d.max_cfl = do_push ? static_cast<double>(__uint_as_float(S->max_cfl_bits)) : 0.0;
+    d.pad = 0.0;
+    long long nl[kSpecies];
+    for (int s = 0; s < kSpecies; ++s) {
+      for (int e = 0; e < 2; ++e)
+        d.absorbed[e][s] = do_push ? static_cast<int64_t>(S->absorbed[e][s]) : 0;
+      nl[s] = S->n_live[s] - d.absorbed[0][s] - d.absorbed[1][s];
+    }
+    d.emitted[0] = do_push ? static_cast<int64_t>(S->emitted[0]) : 0;
+    d.emitted[1] = do_push ? static_cast<int64_t>(S->emitted[1]) : 0;
+    d.injected = do_push ? static_cast<int64_t>(S->injected) : 0;
+    nl[1] += d.injected;
+    nl[2] += d.emitted[0] + d.emitted[1];
+    for (int s = 0; s < kSpecies; ++s) d.n_live[s] = nl[s];
+    d.conv_count = conv;
+    S->cur = d;
+    if (level < B.hist_rows) B.hist[level] = d;
+
+    // commit the circuit and surface-charge state of the new level
+    S->sigma = sigma_n;
+    S->Qh[3] = Q3;
+    S->Qh[2] = Q2;
+    S->Qh[1] = Q1;
+    S->Qh[0] = Qn;
+    S->level = level;
+    if (do_push) S->pushed = 1;
+    for (int s = 0; s < kSpecies; ++s) {
+      S->n_live[s] = nl[s];
+      for (int e = 0; e < 2; ++e) S->absorbed[e][s] = 0ULL;
+    }
+    S->emitted[0] = S->emitted[1] = 0ULL;
+    S->injected = 0ULL;
+    S->conv_count = 0;
+    S->ion_energy_q = 0;
+    S->max_cfl_bits = 0u;
+    if (status != 0 && S->status == 0) S->status = status;
+  }
+  // the next push processes the slots in use, rounded up to whole vectors;
+  // the padding slots are made dead here
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + kSpecies) {
+    const int s = threadIdx.x - 32;
+    long long na = static_cast<long long>(S->n_alloc[s]);
+    if (na > P->cap[s]) na = P->cap[s];
+    const long long na4 = (na + 3) & ~3LL;
+    real* xs = reinterpret_cast<real*>(S->xi[s]);
+    real* us = reinterpret_cast<real*>(S->u[s]);
+    for (long long k = na; k < na4; ++k) {
+      xs[k] = real(-1);
+      us[k] = real(0);
+    }
+    S->n_alloc[s] = na4;
+    S->n_proc[s] = na4;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -715,7 +1012,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 // ---------------------------------------------------------------------------
 template <typename real>
 __global__ void __launch_bounds__(kThreads) k_compact(Bufs B) {
-  const DevParams* __restrict__ P = B.P;
   DevState* S = B.S;
   __shared__ unsigned int s_ticket;
   __shared__ int s_stop;
@@ -795,6 +1091,19 @@ __global__ void __launch_bounds__(kThreads) k_compact(Bufs B) {
   }
 }
 
+// polarity V_s(t_n) for n = 0..rows-1, once at set-up (the source of Sec. 2.1)
+__global__ void k_source_table(const DevParams* P, double* vs, int64_t rows) {
+  for (int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; n < rows;
+       n += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    vs[n] = P->polarity * source_voltage(P, static_cast<double>(n) * P->dt);
+}
+
+cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st) {
+  const int grid = static_cast<int>((rows + 255) / 256 < 1024 ? (rows + 255) / 256 : 1024);
+  k_source_table<<<grid, 256, 0, st>>>(P, vs, rows);
+  return cudaGetLastError();
+}
+
 template <typename real>
 __global__ void k_fill(real* p, int64_t n, real v) {
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
@@ -805,34 +1114,66 @@ __global__ void k_fill(real* p, int64_t n, real v) {
 // ---------------------------------------------------------------------------
 // Host-side launchers (internal C++ interface used by cp_api.cu)
 // ---------------------------------------------------------------------------
-size_t step_smem_bytes(int N, int precision) {
+size_t push_smem_bytes(int N, int precision) {
   const size_t es = (precision == CP_FP32) ? sizeof(float) : sizeof(double);
-  const size_t particle = align16(sizeof(long long) * (N + 1)) + es * (N + 2);
-  const size_t solve = sizeof(double) * (3 * static_cast<size_t>(N) + 2);
-  return particle > solve ? particle : solve;
+  return align16(sizeof(long long) * (N + 1)) + align16(sizeof(unsigned int) * 2 * N) +
+         2 * es * (N + 1);
 }
 
-cudaError_t step_configure(int precision, size_t smem) {
-  if (precision == CP_FP32)
-    return cudaFuncSetAttribute(k_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
-  return cudaFuncSetAttribute(k_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(smem));
+size_t solve_smem_bytes(int N) {
+  const size_t chunk = (N + kSolveCtas - 1) / kSolveCtas;
+  return align16(8 * chunk) + 16 * chunk + 4 * 8 * chunk;
 }
 
-cudaError_t step_occupancy(int precision, size_t smem, int* blocks_per_sm) {
-  if (precision == CP_FP32)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step<float>, kThreads, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step<double>, kThreads, smem);
+cudaError_t kernels_configure(int precision, size_t push_smem, size_t solve_smem) {
+  cudaError_t e;
+  if (precision == CP_FP32) {
+    e = cudaFuncSetAttribute(k_push<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(push_smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(solve_smem));
+  } else {
+    e = cudaFuncSetAttribute(k_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(push_smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(solve_smem));
+  }
+  return e;
 }
 
-cudaError_t step_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
-                        int do_push, int mode, double tol) {
+cudaError_t push_occupancy(int precision, size_t smem, int* blocks_per_sm) {
   if (precision == CP_FP32)
-    k_step<float><<<grid, kThreads, smem, st>>>(B, do_push, mode, tol);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<float>, kThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<double>, kThreads, smem);
+}
+
+cudaError_t push_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
+                        int do_push) {
+  if (precision == CP_FP32)
+    k_push<float><<<grid, kThreads, smem, st>>>(B, do_push);
   else
-    k_step<double><<<grid, kThreads, smem, st>>>(B, do_push, mode, tol);
+    k_push<double><<<grid, kThreads, smem, st>>>(B, do_push);
   return cudaGetLastError();
+}
+
+cudaError_t solve_launch(int precision, const Bufs& B, size_t smem, cudaStream_t st, int do_push,
+                         int mode, double tol) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kSolveCtas, 1, 1);
+  cfg.blockDim = dim3(kSolveThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kSolveCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision == CP_FP32) return cudaLaunchKernelEx(&cfg, k_solve<float>, B, do_push, mode, tol);
+  return cudaLaunchKernelEx(&cfg, k_solve<double>, B, do_push, mode, tol);
 }
 
 cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t st) {

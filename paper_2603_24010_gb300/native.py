@@ -215,8 +215,8 @@ def cp_enable_timing(ctx, on):
 
 
 def cp_read_timing(ctx):
-    ms = np.zeros(2)
-    n = np.zeros(2, dtype=np.int64)
+    ms = np.zeros(3)
+    n = np.zeros(3, dtype=np.int64)
     _check("cp_read_timing", lib().cp_read_timing(ctx, _dp(ms), _i64p(n)))
     return ms, n
 
