@@ -220,6 +220,34 @@ int cp_read_timing(cp_ctx* ctx, double ms[3], int64_t n[3]);
    are written.  Errors: CP_ERR_CAPACITY if cap < count. */
 int cp_read_launch_times(cp_ctx* ctx, double* ms, int64_t cap, int64_t* n);
 
+/* Allocation-free push of one FP32 ion population through one step (the
+   paper has no counterpart; this serves callers that cannot call cudaMalloc,
+   e.g. a step inside a real-time loop or a process that must not grow
+   device memory after start-up).  It needs no context: every input and
+   output is a caller-owned device buffer, and the scratch it needs (the
+   list of ions absorbed in the push) is a static device array of 8 MiB that
+   every GPU loading this library holds until the process exits.
+   Computes what one cp_step call does for ions alone: gather of the field E
+   (N FP64 edge values E_{k+1/2}, device), kick (half kick if half_kick != 0)
+   and drift of xi/u (device, FP32 cell units, updated in place; absorbed
+   ions become xi = -1), secondary emission with the Philox draws of
+   (seed, step, id[k]), and the deposit of the surviving ions and the
+   emitted electrons into G (device, N+1 int64, overwritten; 2^16 per
+   macroparticle).  Emitted electrons are written to se_xi/se_u (device,
+   capacity se_cap).  counts (device, 6 int64): ions absorbed at x = 0 and
+   x = d, electrons emitted at x = 0 and x = d, electrons written, and the
+   convection count at x = 0.  The first call on a device looks up the
+   scratch array's address; make that first call before any stream capture.
+   The call synchronises `stream`.  Every call shares the one scratch array:
+   calls that overlap on the GPU (other streams, other host threads) race.
+   Errors: CP_ERR_ARG (null buffer, n_cells outside 2..4096, bad sizes),
+   CP_ERR_CAPACITY (n > 524288 ions, the scratch's limit; or more emitted
+   electrons than se_cap), CP_ERR_CUDA. */
+int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, double dt, uint64_t seed,
+                         int64_t step, int32_t half_kick, const double* E, float* xi, float* u,
+                         const uint32_t* id, int64_t n, int64_t* G, float* se_xi, float* se_u,
+                         int64_t se_cap, int64_t* counts, void* stream);
+
 void cp_destroy(cp_ctx* ctx);
 const char* cp_status_str(int status);
 

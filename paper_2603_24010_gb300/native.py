@@ -24,7 +24,8 @@ UNITS_CELL, UNITS_SI = 0, 1
 EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "cp_read_scalars",
            "cp_read_history", "cp_read_grid", "cp_get_particles", "cp_get_level",
            "cp_save_state", "cp_load_state", "cp_last_launch_count", "cp_enable_timing",
-           "cp_read_timing", "cp_read_launch_times", "cp_destroy", "cp_status_str")
+           "cp_read_timing", "cp_read_launch_times", "cp_push_ions_noalloc", "cp_destroy",
+           "cp_status_str")
 
 
 class CpError(RuntimeError):
@@ -90,6 +91,9 @@ def lib():
         L.cp_enable_timing.argtypes = [vp, C.c_int32]
         L.cp_read_timing.argtypes = [vp, dp, i64p]
         L.cp_read_launch_times.argtypes = [vp, dp, C.c_int64, i64p]
+        L.cp_push_ions_noalloc.argtypes = [C.POINTER(cp_gap), C.POINTER(cp_see_beam), C.c_double,
+                                           C.c_uint64, C.c_int64, C.c_int32, vp, vp, vp, vp,
+                                           C.c_int64, vp, vp, vp, C.c_int64, vp, vp]
         L.cp_destroy.argtypes = [vp]
         L.cp_destroy.restype = None
         L.cp_status_str.argtypes = [C.c_int]
@@ -229,6 +233,14 @@ def cp_read_launch_times(ctx):
     ms = np.zeros(max(n.value, 1))
     _check("cp_read_launch_times", lib().cp_read_launch_times(ctx, _dp(ms), n.value, C.byref(n)))
     return ms[:n.value]
+
+
+def cp_push_ions_noalloc(gap, see, dt, seed, step, half_kick, E, xi, u, ids, n, G, se_xi, se_u,
+                         se_cap, counts, stream=None):
+    """Allocation-free ion push; every buffer argument is a device address (int)."""
+    return lib().cp_push_ions_noalloc(C.byref(gap), C.byref(see), float(dt), int(seed), int(step),
+                                      int(half_kick), E, xi, u, ids, int(n), G, se_xi, se_u,
+                                      int(se_cap), counts, C.c_void_p(stream or 0))
 
 
 def cp_destroy(ctx):
