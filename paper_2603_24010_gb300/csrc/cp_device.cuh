@@ -99,6 +99,7 @@ struct DevState {
   long long conv_count;
   long long ion_energy_q;     // sum of rint(256 E_eV) over ions absorbed at x = 0
   unsigned int max_cfl_bits;  // float bits of max |u| (non-negative floats order as ints)
+  double nxt_Vs, nxt_hist;     // source and BDF2 history of the next level
   unsigned long long compact_n[kSpecies];
   unsigned int compact_done;
   uint32_t beam_id_base;

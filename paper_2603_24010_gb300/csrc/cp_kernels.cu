@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "cp_device.cuh"
 
@@ -189,6 +190,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push(Bufs B, int do_pu
   __shared__ long long s_conv, s_energy;
   __shared__ unsigned int s_cfl;
 
+  cudaGridDependencySynchronize();  // the previous solve (or removal) has completed
+  cudaTriggerProgrammaticLaunchCompletion();
   if (threadIdx.x == 0) {
     s_flag[0] = (ldcg(&S->status) != 0);
     s_flag[1] = 0;
@@ -628,11 +631,53 @@ __device__ void cluster_tri_solve_f64(double* v, int lo, int m, int N, double b0
 //   C  per-rank maxima of |r|, |x|, |b| -> backward error
 //   D  keeps every rank's shared memory alive until all remote reads are done
 // ---------------------------------------------------------------------------
-struct SolveSlotA {
-  __int128 uloc;  // sum over the chunk of the chunk-local charge prefix
-  long long tg;   // sum over the chunk of G_i (i >= 1)
-  long long m;    // rows in the chunk
+// Scan segment of the charge grid: s1 = sum of G_i, s2 = sum over the
+// segment of the inclusive prefix of G within the segment, len = rows.
+// "a then b" is associative: (a1 + b1, a2 + b2 + len_b a1, len_a + len_b).
+struct Seg {
+  __int128 s2;
+  long long s1;
+  long long len;
 };
+
+__device__ __forceinline__ Seg seg_then(const Seg& a, const Seg& b) {
+  Seg r;
+  r.s1 = a.s1 + b.s1;
+  r.s2 = a.s2 + b.s2 + static_cast<__int128>(b.len) * a.s1;
+  r.len = a.len + b.len;
+  return r;
+}
+
+__device__ __forceinline__ Seg shfl_up_seg(const Seg& v, int o) {
+  Seg r;
+  r.s1 = __shfl_up_sync(0xffffffffu, v.s1, o);
+  r.len = __shfl_up_sync(0xffffffffu, v.len, o);
+  r.s2 = shfl_up_t(v.s2, o);
+  return r;
+}
+
+__device__ __forceinline__ Seg shfl_seg(const Seg& v, int src) {
+  Seg r;
+  r.s1 = __shfl_sync(0xffffffffu, v.s1, src);
+  r.len = __shfl_sync(0xffffffffu, v.len, src);
+  const unsigned long long lo = static_cast<unsigned long long>(v.s2);
+  const unsigned long long hi = static_cast<unsigned long long>(static_cast<unsigned __int128>(v.s2) >> 64);
+  const unsigned long long l2 = __shfl_sync(0xffffffffu, lo, src);
+  const unsigned long long h2 = __shfl_sync(0xffffffffu, hi, src);
+  r.s2 = static_cast<__int128>((static_cast<unsigned __int128>(h2) << 64) | l2);
+  return r;
+}
+
+// Inclusive warp scan of segments (Kogge-Stone with the "then" operator).
+__device__ __forceinline__ Seg warp_scan_seg(Seg v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Seg y = shfl_up_seg(v, o);
+    if (static_cast<int>(lane_id()) >= o) v = seg_then(y, v);
+  }
+  return v;
+}
+
 struct SolveSlotB {
   double first_phi, last_phi, first_E, phi0;
 };
@@ -682,20 +727,21 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
   const DevParams* P = B.P;
   DevState* S = B.S;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(16) __int128 w128[32];
-  __shared__ long long w64[32];
+  __shared__ __align__(16) Seg wseg[32];
+  __shared__ __align__(16) Seg slotA;
+  __shared__ __align__(16) Seg s_rank_off;
+  __shared__ __align__(16) Seg s_next_off;
+  __shared__ __align__(16) __int128 s_U;
   __shared__ double wd[3][32];
   __shared__ unsigned long long wu[3][32];
   __shared__ double s_eta;
-  __shared__ __align__(16) SolveSlotA slotA;
   __shared__ SolveSlotB slotB;
   __shared__ SolveSlotC slotC;
   __shared__ double slotd;
-  __shared__ __align__(16) __int128 s_offP, s_U;
-  __shared__ long long s_offS;
   __shared__ double sc[24];
   __shared__ int s_stop;
 
+  cudaGridDependencySynchronize();  // the push that deposited G has completed
   if (threadIdx.x == 0) s_stop = (ldcg(&S->status) != 0);
   __syncthreads();
   if (s_stop) return;  // the status cannot change while this kernel runs: all ranks agree
@@ -705,72 +751,113 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
   const int lo = min(rank * chunk, N);
   const int hi = min(lo + chunk, N);
   const int m = hi - lo;
-  long long* Sg = reinterpret_cast<long long*>(smem);                      // chunk
-  __int128* Pq = reinterpret_cast<__int128*>(smem + align16(8 * chunk));   // chunk
-  double* ph = reinterpret_cast<double*>(smem + align16(8 * chunk) + 16 * chunk);
+  long long* Gv = reinterpret_cast<long long*>(smem);  // chunk: G_i of this rank's rows
+  double* ph = reinterpret_cast<double*>(smem + align16(8 * chunk));
   double* Ee = ph + chunk;
   double* bb = Ee + chunk;
   double* rr = bb + chunk;
 
+  cudaTriggerProgrammaticLaunchCompletion();
   const long long G0 = ldcg(&B.G[0]);
+  // G of the next chunk's first row (for the field E_hi of the gather table)
+  const long long Gnext = (hi < N) ? ldcg(&B.G[hi]) : 0LL;
   for (int k = threadIdx.x; k < m; k += kSolveThreads) {
     const int i = lo + k;
     const long long g = ldcg(&B.G[i]);
-    Sg[k] = (i == 0) ? 0LL : g;
+    Gv[k] = (i == 0) ? 0LL : g;  // the prefix S'_i = sum_{j=1..i} G_j leaves G_0 out
     B.Glast[i] = g;
-    if (i > 0) B.G[i] = 0;  // G_0 is cleared after every rank has read it
+    if (k > 0) B.G[i] = 0;  // a chunk's first row (and G_0) is cleared after barrier A
   }
   const bool last_rows = (hi == N && m > 0);  // this rank owns row N-1 (and node N)
   if (last_rows && threadIdx.x == 0) {
     B.Glast[N] = ldcg(&B.G[N]);
     B.G[N] = 0;
   }
-  // chunk-local exact prefixes: Sg = inclusive prefix of G_i (i >= 1),
-  // Pq = inclusive prefix of Sg
-  const long long tg = cta_scan(Sg, m, false, w64);
-  for (int k = threadIdx.x; k < m; k += kSolveThreads) Pq[k] = static_cast<__int128>(Sg[k]);
   __syncthreads();
-  const __int128 uloc = cta_scan(Pq, m, false, w128);
-
-  // --- barrier A: offsets of the global prefixes -----------------------------
+  // this thread's run of rows and its segment totals
+  const int per = (m + kSolveThreads - 1) / kSolveThreads;
+  const int r0 = min(static_cast<int>(threadIdx.x) * per, m);
+  const int r1 = min(r0 + per, m);
+  Seg mine;
+  mine.s1 = 0;
+  mine.s2 = 0;
+  mine.len = r1 - r0;
+  for (int k = r0; k < r1; ++k) {
+    mine.s1 += Gv[k];
+    mine.s2 += mine.s1;
+  }
+  const Seg incl = warp_scan_seg(mine);
+  Seg wexcl = shfl_up_seg(incl, 1);  // exclusive within the warp
+  if (lane_id() == 0) {
+    wexcl.s1 = 0;
+    wexcl.s2 = 0;
+    wexcl.len = 0;
+  }
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 31) wseg[w] = incl;
+  __syncthreads();
+  Seg bexcl;  // everything of this CTA before this warp
+  bexcl.s1 = 0;
+  bexcl.s2 = 0;
+  bexcl.len = 0;
+  for (int q = 0; q < w; ++q) bexcl = seg_then(bexcl, wseg[q]);
+  // --- barrier A: the CTAs' totals give every rank its offset ----------------
   if (threadIdx.x == 0) {
-    slotA.uloc = uloc;
-    slotA.tg = tg;
-    slotA.m = m;
+    Seg tot = bexcl;
+    for (int q = w; q < kSolveThreads / 32; ++q) tot = seg_then(tot, wseg[q]);
+    slotA = tot;
   }
   cl.sync();
-  if (threadIdx.x == 0) {
-    long long offS_r = 0, my_offS = 0;
-    __int128 acc = 0, my_offP = 0;
-    for (int r = 0; r < nr; ++r) {
-      const SolveSlotA* q = cl.map_shared_rank(&slotA, r);
-      if (r == rank) {
-        my_offS = offS_r;
-        my_offP = acc;
-      }
-      // sum over rank r's rows of S'_i = its local sum + m_r * (charge before it)
-      acc += q->uloc + static_cast<__int128>(q->m) * offS_r;
-      offS_r += q->tg;
+  if (threadIdx.x < 32) {  // lane q reads rank q; a warp scan gives the offsets
+    Seg v;
+    v.s1 = 0;
+    v.s2 = 0;
+    v.len = 0;
+    if (static_cast<int>(threadIdx.x) < nr) v = *cl.map_shared_rank(&slotA, static_cast<int>(threadIdx.x));
+    Seg ci = v;  // inclusive scan over the (at most 8) ranks
+#pragma unroll
+    for (int o = 1; o < kSolveCtas; o <<= 1) {
+      const Seg y = shfl_up_seg(ci, o);
+      if (static_cast<int>(lane_id()) >= o) ci = seg_then(y, ci);
     }
-    s_offS = my_offS;
-    s_offP = my_offP;
-    s_U = acc;
-    if (rank == 0) B.G[0] = 0;
+    Seg ce = shfl_up_seg(ci, 1);
+    if (threadIdx.x == 0) {
+      ce.s1 = 0;
+      ce.s2 = 0;
+      ce.len = 0;
+    }
+    const Seg mine_off = shfl_seg(ce, rank);
+    const Seg next_off = shfl_seg(ci, rank);  // everything up to and including this rank
+    const Seg all = shfl_seg(ci, nr - 1);
+    if (threadIdx.x == 0) {
+      s_rank_off = mine_off;
+      s_next_off = next_off;
+      s_U = all.s2;
+      if (m > 0) B.G[lo] = 0;
+    }
   }
   __syncthreads();
-  const long long offS = s_offS;
-  const __int128 offP = s_offP, U = s_U;
-
+  const __int128 U = s_U;
+  // offset of everything before this thread's run: rank, then warp, then lane
+  const Seg off = seg_then(seg_then(s_rank_off, bexcl), wexcl);
   // circuit row (every rank evaluates the same scalars)
   if (threadIdx.x == 0) {
     const double dt = P->dt, dx = P->dx, A = P->area, eps0 = P->eps0;
     const double qw = P->e * P->weight;
     const long long conv = do_push ? ldcg(&S->conv_count) : 0LL;
-    const int64_t lev = ldcg(&S->level) + (do_push ? 1 : 0);
-    const double Vs = B.vs[lev];
     const double Q1 = ldcg(&S->Qh[0]), Q2 = ldcg(&S->Qh[1]);
-    const double Q3 = ldcg(&S->Qh[2]), Q4 = ldcg(&S->Qh[3]);
-    const double hist = P->L4dt2 * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) + P->R2dt * (4.0 * Q1 - Q2);
+    const double Q3 = ldcg(&S->Qh[2]);
+    // source and BDF2 history of the new level: precomputed by the previous
+    // solve (circuit_next) except for the first solve of a run
+    double Vs, hist;
+    if (do_push) {
+      Vs = ldcg(&S->nxt_Vs);
+      hist = ldcg(&S->nxt_hist);
+    } else {
+      Vs = B.vs[ldcg(&S->level)];
+      const double Q4 = ldcg(&S->Qh[3]);
+      hist = P->L4dt2 * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) + P->R2dt * (4.0 * Q1 - Q2);
+    }
     double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
     if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
       if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
@@ -800,33 +887,37 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
   const double alpha = P->alpha, inv_dx = P->inv_dx;
   const double E0 = D0 * inv_dx, Ea = alpha * inv_dx;
   // D_i = D_0 + alpha S'_i;  x_i = (N - i) D_0 + alpha (U - P_i);  E_i = D_i / dx
-  for (int k = threadIdx.x; k < m; k += kSolveThreads) {
-    const int i = lo + k;
-    const long long Si = offS + Sg[k];
-    // exclusive global prefix of S' at row i
-    const __int128 Pi = offP + static_cast<__int128>(k) * offS + (Pq[k] - static_cast<__int128>(Sg[k]));
-    ph[k] = fma(static_cast<double>(N - i), D0, alpha * i128_to_double(U - Pi));
-    Ee[k] = fma(Ea, static_cast<double>(Si), E0);
-    const long long gi = (k == 0) ? Sg[0] : (Sg[k] - Sg[k - 1]);
-    bb[k] = (i == 0) ? b0 : -alpha * static_cast<double>(gi);
+  {
+    long long S = off.s1;       // S'_i, running over the run
+    __int128 Pex = off.s2;      // P_i = sum_{k<i} S'_k (exclusive)
+    for (int k = r0; k < r1; ++k) {
+      const int i = lo + k;
+      S += Gv[k];
+      ph[k] = fma(static_cast<double>(N - i), D0, alpha * i128_to_double(U - Pex));
+      Ee[k] = fma(Ea, static_cast<double>(S), E0);
+      bb[k] = (i == 0) ? b0 : -alpha * static_cast<double>(Gv[k]);
+      Pex += S;
+    }
   }
   __syncthreads();
 
   const bool strict_rlc = (P->circuit == CP_CIRCUIT_SERIES_RLC && mode == 0);
-  double eta = 0.0, nextE = 0.0;
+  // The neighbouring chunks' edge values follow from the exact prefixes with
+  // the same arithmetic their owners use, so no exchange is needed:
+  // x_{lo-1} needs P_{lo-1} = P_lo - S'_{lo-1}; x_hi needs P_hi; E_hi needs S'_hi.
+  const Seg ro = s_rank_off, no = s_next_off;
+  double prev_phi = 0.0, next_phi = 0.0, nextE = 0.0;
+  if (lo > 0)
+    prev_phi = fma(static_cast<double>(N - (lo - 1)), D0,
+                   alpha * i128_to_double(U - (ro.s2 - static_cast<__int128>(ro.s1))));
+  if (hi < N) {
+    next_phi = fma(static_cast<double>(N - hi), D0, alpha * i128_to_double(U - no.s2));
+    nextE = fma(Ea, static_cast<double>(no.s1 + Gnext), E0);
+  }
+  const double phi0 = fma(static_cast<double>(N), D0, alpha * i128_to_double(U));  // row 0's x_0
+  double eta = 0.0;
+  cg::cluster_group::arrival_token done_tok;
   for (int sweep = 0; sweep <= 3; ++sweep) {
-    // --- barrier B: edge values of the neighbouring chunks -------------------
-    if (threadIdx.x == 0 && m > 0) {
-      slotB.first_phi = ph[0];
-      slotB.last_phi = ph[m - 1];
-      slotB.first_E = Ee[0];
-      slotB.phi0 = ph[0];
-    }
-    cl.sync();
-    const double prev_phi = (rank > 0 && m > 0) ? cl.map_shared_rank(&slotB, rank - 1)->last_phi : 0.0;
-    const double next_phi = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_phi : 0.0;
-    nextE = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_E : 0.0;
-    const double phi0 = cl.map_shared_rank(&slotB, 0)->phi0;
     unsigned long long rm = 0ULL, xm = 0ULL, bm = 0ULL;
     for (int k = threadIdx.x; k < m; k += kSolveThreads) {
       const int i = lo + k;
@@ -851,13 +942,25 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
       slotC.bmax = bm;
     }
     cl.sync();
-    if (threadIdx.x == 0) {
-      for (int r = 0; r < nr; ++r) {
-        const SolveSlotC* q = cl.map_shared_rank(&slotC, r);
-        rm = max(rm, q->rmax);
-        xm = max(xm, q->xmax);
-        bm = max(bm, q->bmax);
+    if (threadIdx.x < 32) {  // lane q reads rank q
+      unsigned long long a = 0, b = 0, c = 0;
+      if (static_cast<int>(threadIdx.x) < nr) {
+        const SolveSlotC* q = cl.map_shared_rank(&slotC, static_cast<int>(threadIdx.x));
+        a = q->rmax;
+        b = q->xmax;
+        c = q->bmax;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+      }
+      rm = a;
+      xm = b;
+      bm = c;
+    }
+    if (threadIdx.x == 0) {
       const double rmd = __longlong_as_double(static_cast<long long>(rm));
       const double xmd = __longlong_as_double(static_cast<long long>(xm));
       const double bmd = __longlong_as_double(static_cast<long long>(bm));
@@ -865,16 +968,20 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
       const double den = nA * xmd + bmd;
       double e = den > 0.0 ? rmd / den : 0.0;
       if (strict_rlc) {  // the circuit row with the potential of row 0
-        const double Qn = sc[3] - sc[2] * phi0;
-        const double kvl = P->a21 * Qn - (sc[4] + sc[5]) + phi0;
-        const double kden = P->a21 * fabs(Qn) + fabs(sc[4] + sc[5]) + fabs(phi0);
+        const double p0 = sweep ? sc[13] : phi0;
+        const double Qn = sc[3] - sc[2] * p0;
+        const double kvl = P->a21 * Qn - (sc[4] + sc[5]) + p0;
+        const double kden = P->a21 * fabs(Qn) + fabs(sc[4] + sc[5]) + fabs(p0);
         if (kden > 0.0) e = fmax(e, fabs(kvl) / kden);
       }
       s_eta = e;
     }
     __syncthreads();
     eta = s_eta;
-    if (!(eta > tol) || sweep == 3) break;
+    if (!(eta > tol) || sweep == 3) {
+      done_tok = cl.barrier_arrive();  // this rank's remote reads are done
+      break;
+    }
     // refinement: solve A delta = r, x -= delta (FP64; rare path)
     const double r0 = (rank == 0) ? rr[0] : 0.0;
     if (rank == 0 && threadIdx.x == 0) sc[14] = r0;
@@ -883,12 +990,22 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     cluster_tri_solve_f64(rr, lo, m, N, r0all, gam, wd[0], &slotd, sc + 16);
     for (int k = threadIdx.x; k < m; k += kSolveThreads) ph[k] -= rr[k];
     __syncthreads();
-    if (threadIdx.x == 0 && m > 0) slotB.first_phi = ph[0];
+    // refined edges: exchange them (rare path)
+    if (threadIdx.x == 0 && m > 0) {
+      slotB.first_phi = ph[0];
+      slotB.last_phi = ph[m - 1];
+    }
     cl.sync();
-    const double np = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_phi : 0.0;
+    next_phi = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_phi : 0.0;
+    prev_phi = (lo > 0) ? cl.map_shared_rank(&slotB, rank - 1)->last_phi : 0.0;
+    const double phi0_new = cl.map_shared_rank(&slotB, 0)->first_phi;
     for (int k = threadIdx.x; k < m; k += kSolveThreads)
-      Ee[k] = (ph[k] - ((k + 1 < m) ? ph[k + 1] : np)) * inv_dx;
+      Ee[k] = (ph[k] - ((k + 1 < m) ? ph[k + 1] : next_phi)) * inv_dx;
     __syncthreads();
+    if (threadIdx.x == 0 && m > 0) slotB.first_E = Ee[0];
+    cl.sync();
+    nextE = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_E : 0.0;
+    sc[13] = phi0_new;
   }
 
   // outputs; the gather table pairs need the next chunk's first field value
@@ -911,7 +1028,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     }
   }
   if (last_rows && threadIdx.x == 0) B.phi[N] = 0.0;
-  cl.sync();  // barrier D: keep every rank's shared memory alive until all remote reads are done
+  // barrier D: no rank leaves (freeing its shared memory) before every
+  // rank's remote reads are done
+  cl.barrier_wait(std::move(done_tok));
   if (rank != 0) return;
 
   if (threadIdx.x == 0) {
@@ -974,6 +1093,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     S->Qh[2] = Q2;
     S->Qh[1] = Q1;
     S->Qh[0] = Qn;
+    // source and BDF2 history of the next level (off the next solve's critical path)
+    S->nxt_Vs = (level + 1 < B.hist_rows + 1) ? B.vs[level + 1] : 0.0;
+    S->nxt_hist = P->L4dt2 * (24.0 * Qn - 22.0 * Q1 + 8.0 * Q2 - Q3) + P->R2dt * (4.0 * Qn - Q1);
     S->level = level;
     if (do_push) S->pushed = 1;
     for (int s = 0; s < kSpecies; ++s) {
@@ -1122,7 +1244,7 @@ size_t push_smem_bytes(int N, int precision) {
 
 size_t solve_smem_bytes(int N) {
   const size_t chunk = (N + kSolveCtas - 1) / kSolveCtas;
-  return align16(8 * chunk) + 16 * chunk + 4 * 8 * chunk;
+  return align16(8 * chunk) + 4 * 8 * chunk;
 }
 
 cudaError_t kernels_configure(int precision, size_t push_smem, size_t solve_smem) {
@@ -1149,13 +1271,23 @@ cudaError_t push_occupancy(int precision, size_t smem, int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<double>, kThreads, smem);
 }
 
+// Push and solve are launched with programmatic dependent launch: each may
+// be scheduled while its predecessor finishes and waits in
+// cudaGridDependencySynchronize() until that grid has completed.
 cudaError_t push_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
                         int do_push) {
-  if (precision == CP_FP32)
-    k_push<float><<<grid, kThreads, smem, st>>>(B, do_push);
-  else
-    k_push<double><<<grid, kThreads, smem, st>>>(B, do_push);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision == CP_FP32) return cudaLaunchKernelEx(&cfg, k_push<float>, B, do_push);
+  return cudaLaunchKernelEx(&cfg, k_push<double>, B, do_push);
 }
 
 cudaError_t solve_launch(int precision, const Bufs& B, size_t smem, cudaStream_t st, int do_push,
@@ -1165,13 +1297,15 @@ cudaError_t solve_launch(int precision, const Bufs& B, size_t smem, cudaStream_t
   cfg.blockDim = dim3(kSolveThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kSolveCtas;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   if (precision == CP_FP32) return cudaLaunchKernelEx(&cfg, k_solve<float>, B, do_push, mode, tol);
   return cudaLaunchKernelEx(&cfg, k_solve<double>, B, do_push, mode, tol);
 }
