@@ -36,12 +36,51 @@ METRIC = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = {W.FP32: 16, W.FP64: 32}  # read + write of (xi, u)
 
 
-def workload(name, seed):
+def workload(name, seed, pairs=None):
     if name == "gap_1d_fp32_large":
-        return W.gap_1d_fp32_large(seed)
-    if name == "gap_1d_fp64":
-        return W.gap_1d_fp64(seed)
-    raise SystemExit("unknown workload " + name)
+        cfg = W.gap_1d_fp32_large(seed)
+    elif name == "gap_1d_fp64":
+        cfg = W.gap_1d_fp64(seed)
+    else:
+        raise SystemExit("unknown workload " + name)
+    if pairs:  # same density and physics with a different number of macroparticles
+        cfg["weight"] = cfg["weight"] * cfg["n_pairs"] / pairs
+        cfg["n_pairs"] = int(pairs)
+    return cfg
+
+
+PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_gap_1d_fp32_large.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2603_24010_gb300", "csrc", f)
+                  for f in ("cp_push.cu", "cp_common.cuh", "cp_device.cuh")]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_dram_bytes_per_particle():
+    """DRAM bytes per particle-step of the push kernel from the committed ncu
+    summary, or None when the kernel sources changed since it was taken."""
+    try:
+        text = open(PUSH_PROFILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith(("dram_bytes_per_particle_step", "source_sha256")):
+            k, v = line.strip().split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_particle_step"])
+    except (KeyError, ValueError):
+        return None
 
 
 def workload_desc(cfg, K, W_):
@@ -128,7 +167,7 @@ def run_native(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    cfg = workload(args.workload, seed=args.seed + rank)
+    cfg = workload(args.workload, seed=args.seed + rank, pairs=args.pairs)
     K, Wm = args.steps, args.warmup
     total_steps = Wm + K
     xe, ue, xI, ui = load_particles(cfg, cfg["seed"])
@@ -160,6 +199,8 @@ def run_native(args, rank, world):
     live = hist["n_live"].sum(axis=1)
     psteps = int(live.sum())
     g.close()
+    if args.single:  # one graph pass only (used under ncu)
+        return dict(cfg=cfg, ms=ms, psteps=psteps, launches=launches, clocks=clk)
 
     # ---- the same run with per-launch CUDA events (direct launches) --------
     # gives each kernel's device time for the roofline
@@ -220,10 +261,12 @@ def run_native(args, rank, world):
     sel_ms = float(np.asarray(per_launch_ms)[sel[:len(per_launch_ms)]].sum())
     avg_launch_ms = sel_ms / n_sel
     achieved = bpp * float(live[sel].sum()) / (sel_ms * 1e-3) / 1e9
+    dbpp = profiled_dram_bytes_per_particle() if cfg["precision"] == W.FP32 else None
+    traffic = dbpp * float(live[sel].sum()) / n_sel if dbpp else None
     return dict(cfg=cfg, ms=ms, ms_timed=ms_timed, psteps=psteps, e2e_ms=e2e_ms, e2e_psteps=e2e_psteps, h2d=h2d,
                 d2h=d2h, launches=launches, kernel_ms=kms.tolist(), kernel_n=kn.tolist(),
                 avg_launch_ms=avg_launch_ms, achieved=achieved, peak=peak, peak_kind=peak_kind,
-                clocks=clk, bpp=bpp, n_sel=n_sel, frac_psteps_above_l2=float(live[state > 129e6].sum()) / max(psteps, 1))
+                clocks=clk, bpp=bpp, n_sel=n_sel, traffic=traffic, frac_psteps_above_l2=float(live[state > 129e6].sum()) / max(psteps, 1))
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -267,12 +310,16 @@ def main():
     ap.add_argument("--workload", default="gap_1d_fp32_large")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="override the workload's loaded pairs (weight scaled to keep the density)")
+    ap.add_argument("--single", action="store_true",
+                    help="only the device-resident graph pass (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    cfg = workload(args.workload, args.seed)
+    cfg = workload(args.workload, args.seed, pairs=args.pairs)
     config = {"workload": workload_desc(cfg, args.steps, args.warmup),
               "l2": ("inputs larger than L2 for the roofline launches (particle state > 1.5 x "
                      "129 MB); the state starts at %.0f MB and grows with the beam, no flush"
@@ -298,6 +345,12 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     r = run_native(args, rank, world)
+    if args.single:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": r["psteps"] / (r["ms"] * 1e-3),
+                              "unit": "particle-steps/s", "steps": args.steps,
+                              "config": config, "note": "single graph pass (profiling run)"}))
+        return
     if rank != 0:
         if world > 1:
             import torch
@@ -320,7 +373,7 @@ def main():
                 "h2d_bytes_per_step": r["h2d"] / K, "d2h_bytes_per_step": r["d2h"] / K},
         "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
-                     "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": None,
+                     "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": r["traffic"],
                      "kernel": "k_push", "peak_source": r["peak_kind"],
                      "avg_launch_ms": r["avg_launch_ms"], "launches_used": r["n_sel"],
                      "bytes_per_particle_step": r["bpp"],

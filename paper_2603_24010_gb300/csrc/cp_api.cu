@@ -18,13 +18,15 @@
 
 namespace cpk {
 size_t push_smem_bytes(int N, int precision);
-size_t solve_smem_bytes(int N);
-cudaError_t kernels_configure(int precision, size_t push_smem, size_t solve_smem);
+size_t solve_smem_bytes(int N, int ctas);
+cudaError_t solve_cluster_size(int precision, int N, int* ctas);
+cudaError_t push_configure(int precision, size_t push_smem);
+cudaError_t solve_configure(int precision, size_t solve_smem);
 cudaError_t push_occupancy(int precision, size_t smem, int* blocks_per_sm);
 cudaError_t push_launch(int precision, const Bufs& B, int grid, size_t smem, cudaStream_t st,
                         int do_push);
-cudaError_t solve_launch(int precision, const Bufs& B, size_t smem, cudaStream_t st, int do_push,
-                         int mode, double tol);
+cudaError_t solve_launch(int precision, const Bufs& B, int ctas, size_t smem, cudaStream_t st,
+                         int do_push, int mode, double tol);
 cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t st);
 cudaError_t fill_launch(int precision, void* p, int64_t n, double v, cudaStream_t st);
 cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st);
@@ -59,6 +61,7 @@ struct cp_ctx {
   int grid = 0;
   size_t smem = 0;        // push kernel
   size_t solve_smem = 0;  // solve kernel
+  int solve_ctas = 8;     // CTAs in the solve's cluster
   bool initialized = false;
   int compact_every = 64;
   int since_compact = 0;
@@ -205,8 +208,10 @@ int initialize(cp_ctx* c, int mode, double tol) {
 
   // launch shape: persistent grid of resident push CTAs, one solve cluster
   c->smem = cpk::push_smem_bytes(c->N, c->precision);
-  c->solve_smem = cpk::solve_smem_bytes(c->N);
-  CP_CUDA(cpk::kernels_configure(c->precision, c->smem, c->solve_smem));
+  CP_CUDA(cpk::solve_cluster_size(c->precision, c->N, &c->solve_ctas));
+  c->solve_smem = cpk::solve_smem_bytes(c->N, c->solve_ctas);
+  CP_CUDA(cpk::push_configure(c->precision, c->smem));
+  CP_CUDA(cpk::solve_configure(c->precision, c->solve_smem));
   int per_sm = 0, sms = 0;
   CP_CUDA(cpk::push_occupancy(c->precision, c->smem, &per_sm));
   CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -247,7 +252,7 @@ int initialize(cp_ctx* c, int mode, double tol) {
   // deposit rho^0 and solve level 0
   const cpk::Bufs B0 = make_bufs(c);
   CP_CUDA(cpk::push_launch(c->precision, B0, c->grid, c->smem, c->stream, 0));
-  CP_CUDA(cpk::solve_launch(c->precision, B0, c->solve_smem, c->stream, 0, mode, tol));
+  CP_CUDA(cpk::solve_launch(c->precision, B0, c->solve_ctas, c->solve_smem, c->stream, 0, mode, tol));
   c->launches += 2;
   return CP_OK;
 }
@@ -272,7 +277,7 @@ int build_graph(cp_ctx* c, int mode, double tol) {
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < c->compact_every && e == cudaSuccess; ++k) {
     e = cpk::push_launch(c->precision, B, c->grid, c->smem, c->cap_stream, 1);
-    if (e == cudaSuccess) e = cpk::solve_launch(c->precision, B, c->solve_smem, c->cap_stream, 1, mode, tol);
+    if (e == cudaSuccess) e = cpk::solve_launch(c->precision, B, c->solve_ctas, c->solve_smem, c->cap_stream, 1, mode, tol);
   }
   if (e == cudaSuccess) e = cpk::compact_launch(c->precision, B, c->grid, c->cap_stream);
   const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
@@ -300,7 +305,7 @@ int timed_launch(cp_ctx* c, int which, int mode, double tol, std::vector<std::pa
   if (which == 0)
     CP_CUDA(cpk::push_launch(c->precision, B, c->grid, c->smem, c->stream, 1));
   else if (which == 1)
-    CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_smem, c->stream, 1, mode, tol));
+    CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_ctas, c->solve_smem, c->stream, 1, mode, tol));
   else
     CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
   CP_CUDA(cudaEventRecord(c->ev_pool[k + 1], c->stream));
@@ -357,7 +362,7 @@ int do_steps(cp_ctx* c, int mode, int32_t n_steps, double tol) {
       continue;
     }
     CP_CUDA(cpk::push_launch(c->precision, B, c->grid, c->smem, c->stream, 1));
-    CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_smem, c->stream, 1, mode, tol));
+    CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_ctas, c->solve_smem, c->stream, 1, mode, tol));
     c->launches += 2;
     --left;
     if (++c->since_compact == c->compact_every) {

@@ -34,7 +34,8 @@ constexpr int kCtasPerSm = 2;          // resident push CTAs per SM
 constexpr int kPerThread = 4;          // particles per thread per tile (one 16 B vector for FP32)
 constexpr int kTile = kThreads * kPerThread;  // particles per CTA tile
 constexpr int kFlushTiles = 31;        // tiles between flushes of the 32-bit cell sums
-constexpr int kSolveCtas = 8;          // CTAs (one cluster) of the coupled solve
+constexpr int kSolveCtas = 8;          // CTAs (one cluster) of the coupled solve (portable)
+constexpr int kSolveCtasMax = 16;      // non-portable cluster size used where the GPU allows it
 constexpr int kSolveThreads = 512;
 constexpr double kFix = 65536.0;       // fixed-point units per macroparticle charge
 constexpr uint64_t kTagSee = 0x5345ULL;
