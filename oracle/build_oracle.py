@@ -8,18 +8,18 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "cp_oracle.c")
+SRCS = [os.path.join(HERE, "cp_oracle.c"), os.path.join(HERE, "or_mlp.c")]
 HDR = os.path.join(HERE, "cp_oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    newest = max(os.path.getmtime(f) for f in SRCS + [HDR])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
-           "-shared", "-Wall", "-o", tmp, SRC, "-lm"]
+           "-shared", "-Wall", "-o", tmp, *SRCS, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -183,8 +183,8 @@ static double row_apply(int64_t N, double b0, const double* phi, int64_t i) {
 }
 
 static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_t conv_count,
-                      double sigma_prev, const double* Qh, double t, double tol, double* phi,
-                      double* E, or_solve_out* o) {
+                      double sigma_prev, const double* Qh, double phi0_prev, double J_hat,
+                      double t, double tol, double* phi, double* E, or_solve_out* o) {
   const int64_t N = p->n_cells;
   const double dx = p->d / (double)N;
   const double A = p->area;
@@ -211,9 +211,17 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
       Qpart = g * (Vs + hist); /* K */
       gam = g * dx / (eps0 * A);
     } else {
-      /* Weak mode, Sec. 2.4.3: free circuit with its load capacitor C gives
-         Q*^n; it enters Eq. Poisson_BC3 unchanged. */
-      Qpart = (Vs + hist) / (a2 + a1 + 1.0 / p->C);
+      /* Weak mode, Sec. 2.4.3: the circuit alone is advanced one step with
+         its load capacitor C, whose voltage starts from the electrode
+         potential of the previous level (the capacitor state handed back
+         to the circuit solver, Q_4^{n-1} = C phi_0^{n-1}); the circuit keeps
+         its own loop-charge history Q.  KVL of the loop:
+           a Q^n - hist + phi_0^{n-1} + (Q^n - Q^{n-1} + J_hat)/C = V_s,
+         J_hat being a prediction of the plasma's own change of C phi_0 over
+         the step (0 in the plain lagged scheme).  The capacitor charge
+         Q*^n = C phi_0^{n-1} + Q^n - Q^{n-1} enters Eq. Poisson_BC3 against
+         Q_4^{n-1} = C phi_0^{n-1}, i.e. the circuit delivers Q^n - Q^{n-1}. */
+      Qpart = (Vs + hist + Q1 / p->C - phi0_prev - J_hat / p->C) / (a2 + a1 + 1.0 / p->C);
     }
   }
 
@@ -272,14 +280,16 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
     if (!isfinite(phi[i])) return OR_ERR_NONFINITE;
 
   /* Surface-charge update, Eq. top_plate_charge (Eq. sigma_update in strict
-     mode), and the weak-mode overwrite Q^n := C phi_0^n (Sec. 2.4.3). */
+     mode).  Q^n is the circuit's loop charge in both modes; in weak mode the
+     capacitor state for the next level is C phi_0^n (Sec. 2.4.3), carried as
+     the level's phi_0. */
   if (circuit == OR_CIRCUIT_SERIES_RLC && mode == OR_MODE_STRICT) {
     o->Qn = Qpart - g * phi[0];
     o->sigma_n = sigma_prev + (Qconv + o->Qn - Q1) / A;
     o->I = (3.0 * o->Qn - 4.0 * Q1 + Q2) / (2.0 * dt);
   } else if (circuit == OR_CIRCUIT_SERIES_RLC) {
+    o->Qn = Qpart;
     o->sigma_n = sigma_prev + (Qconv + Qpart - Q1) / A;
-    o->Qn = p->C * phi[0];
     o->I = (3.0 * Qpart - 4.0 * Q1 + Q2) / (2.0 * dt);
   } else {
     o->sigma_n = sigma_prev + Qconv / A;
@@ -294,10 +304,12 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
 }
 
 int or_solve_fields(const or_params* p, int32_t mode, const int64_t* G, int64_t conv_count,
-                    double sigma_prev, const double* Qhist, double t, double tol, double* phi,
-                    double* E, double* out) {
+                    double sigma_prev, const double* Qhist, double phi0_prev, double J_hat,
+                    double t, double tol, double* phi, double* E, double* out) {
   or_solve_out o = {0, 0, 0, 0};
-  int rc = solve_core(p, mode, G, conv_count, sigma_prev, Qhist, t, tol, phi, E, &o);
+  if (mode == OR_MODE_WEAK_LEARNED) mode = OR_MODE_WEAK;
+  int rc = solve_core(p, mode, G, conv_count, sigma_prev, Qhist, phi0_prev, J_hat, t, tol, phi,
+                      E, &o);
   out[0] = o.Qn;
   out[1] = o.sigma_n;
   out[2] = o.I;
@@ -324,6 +336,14 @@ struct or_state {
   int64_t level;
   int solved0, pushed;
   uint64_t beam_id_base;
+  /* weak-coupling predictor */
+  int has_pred;
+  float* pred_params;
+  double in_scale[5], out_scale[2], bound;
+  double feat[8][5]; /* feature rows of the last 8 levels, oldest first */
+  int n_feat, pred_ready;
+  double J_pred, err_avg, J_avg;
+  int64_t n_eval;
   or_diag* hist;
   int64_t hist_len, hist_cap;
 };
@@ -373,7 +393,25 @@ void or_destroy(or_state* s) {
   free(s->phi);
   free(s->E);
   free(s->hist);
+  free(s->pred_params);
   free(s);
+}
+
+int or_set_predictor(or_state* s, const float* params, const double in_scale[5],
+                     const double out_scale[2], double bound) {
+  if (!s || !params || !(bound > 0)) return OR_ERR_ARG;
+  for (int f = 0; f < 5; ++f)
+    if (!(in_scale[f] > 0)) return OR_ERR_ARG;
+  for (int o = 0; o < 2; ++o)
+    if (!(out_scale[o] > 0)) return OR_ERR_ARG;
+  if (!s->pred_params) s->pred_params = (float*)malloc(sizeof(float) * OR_MLP_NPARAM);
+  if (!s->pred_params) return OR_ERR_ARG;
+  memcpy(s->pred_params, params, sizeof(float) * OR_MLP_NPARAM);
+  memcpy(s->in_scale, in_scale, sizeof(s->in_scale));
+  memcpy(s->out_scale, out_scale, sizeof(s->out_scale));
+  s->bound = bound;
+  s->has_pred = 1;
+  return OR_OK;
 }
 
 int or_set_particles(or_state* s, int32_t sp, const double* xi, const double* u,
@@ -421,8 +459,50 @@ static int solve_level(or_state* s, int32_t mode, double tol, int64_t conv_count
   double Qhist[4] = {s->Qh[0], s->Qh[1], s->Qh[2], s->Qh[3]};
   or_solve_out o;
   double t = (double)s->level * s->p.dt;
-  int rc = solve_core(&s->p, mode, s->G, conv_count, s->sigma, Qhist, t, tol, s->phi, s->E, &o);
+  /* phi still holds the previous level (0 before the first solve: the
+     circuit starts at rest) */
+  const double phi0_prev = s->phi[0];
+  const double sigma_prev = s->sigma;
+  /* learned weak scheme: the prediction made for this level, if trusted */
+  double J_used = 0.0;
+  if (mode == OR_MODE_WEAK_LEARNED && s->pred_ready && s->n_eval >= 16 &&
+      s->err_avg <= s->bound * s->J_avg)
+    J_used = s->J_pred;
+  const int32_t core_mode = (mode == OR_MODE_STRICT) ? OR_MODE_STRICT : OR_MODE_WEAK;
+  int rc = solve_core(&s->p, core_mode, s->G, conv_count, s->sigma, Qhist, phi0_prev, J_used, t,
+                      tol, s->phi, s->E, &o);
   if (rc == OR_ERR_NONFINITE) return rc;
+  if (s->has_pred) {
+    /* the prediction for this level against the realised J */
+    if (s->pred_ready) {
+      const double J = s->p.C * (s->phi[0] - phi0_prev) - (o.Qn - Qhist[0]);
+      s->err_avg += (fabs(J - s->J_pred) - s->err_avg) / 16.0;
+      s->J_avg += (fabs(J) - s->J_avg) / 16.0;
+      s->n_eval += 1;
+    }
+    s->pred_ready = 0;
+    if (s->solved0) { /* a pushed level: append its features, predict the next */
+      double row[5];
+      row[0] = (double)conv_count * s->p.e * s->p.weight;
+      row[1] = s->phi[0] - phi0_prev;
+      row[2] = o.sigma_n * s->p.area - sigma_prev * s->p.area;
+      row[3] = (double)d->emitted[0];
+      row[4] = d->ion_energy_eV;
+      for (int j = 0; j < 7; ++j)
+        for (int f = 0; f < 5; ++f) s->feat[j][f] = s->feat[j + 1][f];
+      for (int f = 0; f < 5; ++f) s->feat[7][f] = row[f];
+      if (s->n_feat < 8) s->n_feat += 1;
+      if (s->n_feat == 8) {
+        double x[OR_MLP_IN], y[OR_MLP_OUT];
+        for (int j = 0; j < 8; ++j)
+          for (int f = 0; f < 5; ++f) x[5 * j + f] = s->feat[j][f] / s->in_scale[f];
+        or_mlp_forward(s->pred_params, 1, x, y);
+        s->J_pred = s->out_scale[0] * y[0] + s->out_scale[1] * y[1];
+        s->pred_ready = 1;
+      }
+    }
+  }
+  d->J_hat = J_used;
   s->sigma = o.sigma_n;
   s->Qh[3] = s->Qh[2];
   s->Qh[2] = s->Qh[1];
@@ -565,7 +645,9 @@ static int push_level(or_state* s, int64_t* conv_out, or_diag* d) {
 }
 
 int or_step(or_state* s, int32_t mode, int64_t n_steps, double tol) {
-  if (mode != OR_MODE_STRICT && mode != OR_MODE_WEAK) return OR_ERR_ARG;
+  if (mode != OR_MODE_STRICT && mode != OR_MODE_WEAK && mode != OR_MODE_WEAK_LEARNED)
+    return OR_ERR_ARG;
+  if (mode == OR_MODE_WEAK_LEARNED && !s->has_pred) return OR_ERR_ARG;
   int rc = OR_OK;
   if (!s->solved0) {
     deposit_all(s);

@@ -28,6 +28,7 @@
 
 #define OR_MODE_STRICT 0
 #define OR_MODE_WEAK 1
+#define OR_MODE_WEAK_LEARNED 2 /* weak with the predictor's J_hat (or_set_predictor) */
 
 #define OR_CIRCUIT_SERIES_RLC 0 /* series R-L-source into the gap */
 #define OR_CIRCUIT_OPEN 1       /* floating electrode: no circuit charge */
@@ -85,7 +86,7 @@ typedef struct {
   double residual;  /* backward error of the coupled solve */
   double ion_energy_eV; /* energy of ions absorbed at x = 0 during the push */
   double max_cfl;   /* max |u| (cells/step) over the push that produced level n */
-  double pad;
+  double J_hat;     /* learned weak scheme: prediction used at this level, else 0 [C] */
   int64_t absorbed[2][3]; /* [electrode: 0 at x=0, 1 at x=d][species] */
   int64_t emitted[2];     /* secondaries emitted at [x=0, x=d] */
   int64_t injected;       /* beam ions appended */
@@ -129,7 +130,36 @@ int or_read_history(const or_state* s, int64_t first, int64_t n, or_diag* out);
 /* Solve one coupled field problem for a given charge grid and circuit history
    without touching particles (the App. E/F validation cases). */
 int or_solve_fields(const or_params* p, int32_t mode, const int64_t* G, int64_t conv_count,
-                    double sigma_prev, const double* Qhist /*Q^{n-1..n-4}*/, double t,
-                    double tol, double* phi, double* E, double* out /*Q_n,sigma_n,I,resid*/);
+                    double sigma_prev, const double* Qhist /*Q^{n-1..n-4}*/,
+                    double phi0_prev /*weak: capacitor voltage handed to the circuit*/,
+                    double J_hat /*weak: predicted plasma change of C phi_0 (0: plain)*/,
+                    double t, double tol, double* phi, double* E,
+                    double* out /*Q_n,sigma_n,I,resid*/);
+
+/* ---- weak-coupling predictor (or_mlp.c and the learned weak mode) ----
+   The weak scheme lags the strict one by J^n = C (phi_0^n - phi_0^{n-1}) -
+   (Q^n - Q^{n-1}), the plasma's own change of C phi_0 over a step.  A
+   40-64-64-64-2 GELU network with bfloat16 weights predicts it from the
+   last 8 levels' features (Q_conv, phi_0 increment, Q_surf increment,
+   secondaries emitted at x = 0, absorbed ion energy at x = 0), each divided
+   by in_scale of its feature; outputs are Q_conv^{n+1}/out_scale[0] and
+   (J^{n+1} - Q_conv^{n+1})/out_scale[1].  The learned weak mode uses the
+   prediction once 16 predictions have been checked against the realised J
+   and while the running average (weight 1/16) of |J - J_hat| is at most
+   bound times that of |J|; otherwise the plain lagged solve. */
+#define OR_MLP_IN 40
+#define OR_MLP_HIDDEN 64
+#define OR_MLP_OUT 2
+#define OR_MLP_NPARAM 11074
+double or_bf16(float w);
+double or_gelu(double x);
+double or_gelu_grad(double x);
+void or_mlp_forward(const float* params, int64_t n, const double* Xn, double* Yhat);
+void or_mlp_loss_grad(const float* params, int64_t n, const double* Xn, const double* Yn,
+                      double* grad, double* loss);
+void or_adam(int64_t n, double* p, const double* g, double* m, double* v, int64_t t, double lr,
+             double b1, double b2, double eps);
+int or_set_predictor(or_state* s, const float* params, const double in_scale[5],
+                     const double out_scale[2], double bound);
 
 #endif

@@ -11,7 +11,8 @@ import numpy as np
 from . import build_oracle
 
 ELECTRONS, IONS, SECONDARIES = 0, 1, 2
-STRICT, WEAK = 0, 1
+STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
+MLP_IN, MLP_OUT, MLP_NPARAM = 40, 2, 11074
 SERIES_RLC, OPEN = 0, 1
 OK, ERR_ARG, ERR_RESIDUAL, ERR_NONFINITE = 0, -1, -5, -6
 TAG_SEE, TAG_BEAM = 0x5345, 0x4245
@@ -29,7 +30,7 @@ class OrParams(C.Structure):
 class OrDiag(C.Structure):
     _fields_ = [("step", C.c_int64)] + [(n, C.c_double) for n in (
         "t", "V_gap", "I_circ", "Q_surf", "Q_conv", "Q_circ", "V_source", "residual",
-        "ion_energy_eV", "max_cfl", "pad")] + [
+        "ion_energy_eV", "max_cfl", "J_hat")] + [
         ("absorbed", (C.c_int64 * 3) * 2), ("emitted", C.c_int64 * 2), ("injected", C.c_int64),
         ("n_live", C.c_int64 * 3), ("conv_count", C.c_int64)]
 
@@ -78,7 +79,20 @@ def lib():
         L.or_history_len.restype = C.c_int64
         L.or_read_history.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.POINTER(OrDiag)]
         L.or_solve_fields.argtypes = [C.POINTER(OrParams), C.c_int32, ip, C.c_int64, C.c_double,
-                                      dp, C.c_double, C.c_double, dp, dp, dp]
+                                      dp, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp,
+                                      dp]
+        fp = C.POINTER(C.c_float)
+        L.or_bf16.argtypes = [C.c_float]
+        L.or_bf16.restype = C.c_double
+        L.or_gelu.argtypes = [C.c_double]
+        L.or_gelu.restype = C.c_double
+        L.or_gelu_grad.argtypes = [C.c_double]
+        L.or_gelu_grad.restype = C.c_double
+        L.or_mlp_forward.argtypes = [fp, C.c_int64, dp, dp]
+        L.or_mlp_loss_grad.argtypes = [fp, C.c_int64, dp, dp, dp, dp]
+        L.or_adam.argtypes = [C.c_int64, dp, dp, dp, dp, C.c_int64, C.c_double, C.c_double,
+                              C.c_double, C.c_double]
+        L.or_set_predictor.argtypes = [C.c_void_p, fp, dp, dp, C.c_double]
         _lib = L
     return _lib
 
@@ -166,7 +180,8 @@ def see_electron_batch(cfg, id0, n, step):
     return v, fr
 
 
-def solve_fields(cfg, mode, G, conv_count, sigma_prev, Qhist, t, tol=1e-12):
+def solve_fields(cfg, mode, G, conv_count, sigma_prev, Qhist, t, tol=1e-12, phi0_prev=0.0,
+                 J_hat=0.0):
     p = make_params(cfg)
     N = int(cfg["n_cells"])
     G = np.ascontiguousarray(G, dtype=np.int64)
@@ -175,8 +190,51 @@ def solve_fields(cfg, mode, G, conv_count, sigma_prev, Qhist, t, tol=1e-12):
     E = np.zeros(N)
     out = np.zeros(4)
     rc = lib().or_solve_fields(C.byref(p), int(mode), _ip(G), int(conv_count), float(sigma_prev),
-                               _dp(Qh), float(t), float(tol), _dp(phi), _dp(E), _dp(out))
+                               _dp(Qh), float(phi0_prev), float(J_hat), float(t), float(tol),
+                               _dp(phi), _dp(E), _dp(out))
     return rc, phi, E, dict(Q_n=out[0], sigma_n=out[1], I=out[2], residual=out[3])
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def bf16(w):
+    """bfloat16 rounding (nearest, ties to even) of FP32 values, as float64."""
+    w = np.asarray(w, dtype=np.float32)
+    return np.array([lib().or_bf16(float(v)) for v in w.ravel()]).reshape(w.shape)
+
+
+def gelu(x):
+    return lib().or_gelu(float(x))
+
+
+def gelu_grad(x):
+    return lib().or_gelu_grad(float(x))
+
+
+def mlp_forward(params, Xn):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(Xn, dtype=np.float64).reshape(-1, MLP_IN)
+    Y = np.zeros((X.shape[0], MLP_OUT))
+    lib().or_mlp_forward(_fp(p), X.shape[0], _dp(X), _dp(Y))
+    return Y
+
+
+def mlp_loss_grad(params, Xn, Yn):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(Xn, dtype=np.float64).reshape(-1, MLP_IN)
+    Y = np.ascontiguousarray(Yn, dtype=np.float64).reshape(-1, MLP_OUT)
+    g = np.zeros(MLP_NPARAM)
+    loss = np.zeros(1)
+    lib().or_mlp_loss_grad(_fp(p), X.shape[0], _dp(X), _dp(Y), _dp(g), _dp(loss))
+    return float(loss[0]), g
+
+
+def adam(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place FP64 Adam step on float64 arrays."""
+    lib().or_adam(p.size, _dp(p), _dp(np.ascontiguousarray(g, dtype=np.float64)), _dp(m), _dp(v),
+                  int(t), float(lr), float(b1), float(b2), float(eps))
 
 
 class OracleGap:
@@ -211,6 +269,14 @@ class OracleGap:
         rc = lib().or_set_particles(self._s, species, _dp(xi), _dp(u), idp, xi.size)
         if rc != OK:
             raise ValueError("or_set_particles failed: %d" % rc)
+
+    def set_predictor(self, params, in_scale, out_scale, bound):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        si = np.ascontiguousarray(in_scale, dtype=np.float64)
+        so = np.ascontiguousarray(out_scale, dtype=np.float64)
+        rc = lib().or_set_predictor(self._s, _fp(p), _dp(si), _dp(so), float(bound))
+        if rc != OK:
+            raise ValueError("or_set_predictor failed: %d" % rc)
 
     def step(self, mode, n_steps, tol=1e-12):
         return lib().or_step(self._s, int(mode), int(n_steps), float(tol))
@@ -258,8 +324,6 @@ def diag_to_dict(arr):
             m = 2 if name == "emitted" else 3
             out[name] = np.array([[getattr(arr[k], name)[j] for j in range(m)] for k in range(n)],
                                  dtype=np.int64).reshape(n, m)
-        elif name == "pad":
-            continue
         else:
             dt = np.int64 if typ in (C.c_int64,) else np.float64
             out[name] = np.array([getattr(arr[k], name) for k in range(n)], dtype=dt)

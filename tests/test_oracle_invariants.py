@@ -82,15 +82,10 @@ def test_conservation_on_coupled_run(orc, mode):
     conv = ab[:, 0, 1] - ab[:, 0, 0] - ab[:, 0, 2] + h["emitted"][:, 0]
     np.testing.assert_array_equal(h["conv_count"], conv)
     # circuit-delivered charge = surface-charge change - convection charge
-    Qc = h["Q_circ"]
-    if mode == 0:
-        lhs = Qc[-1] - 0.0
-    else:
-        # weak: the circuit's delivered charge each step is Q*^n - Q^{n-1}
-        lhs = None
+    # (Q_circ is the circuit's loop charge in both schemes, zero at rest)
+    lhs = h["Q_circ"][-1]
     rhs = h["Q_surf"][-1] - cfg["sigma0"] * A - qw * conv.sum()
-    if lhs is not None:
-        assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-10 * abs(h["Q_surf"]).max())
+    assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-10 * abs(h["Q_surf"]).max())
 
 
 def test_runs_are_deterministic(orc):

@@ -78,8 +78,10 @@ def test_app_f_weak_keeps_circuit_charge_zero_and_matches_sheet_potential(orc):
     x = np.arange(N + 1) * dx
     want = sheet_density(cfg) * (cfg["d"] - np.maximum(x, 120 * dx)) / cfg["eps0"]
     np.testing.assert_allclose(phi, want, rtol=0, atol=1e-10 * np.max(want))
-    # the weak scheme then sets Q^n := C phi_0
-    assert out["Q_n"] == pytest.approx(cfg["C"] * phi[0], rel=1e-15)
+    # the circuit's loop charge stays zero; the capacitor state handed back
+    # to the circuit for the next level is C phi_0 (Sec. 2.4.3)
+    assert out["Q_n"] == 0.0
+    assert phi[0] > 0.0
 
 
 @pytest.mark.parametrize("xi0", [0.37, 1.0, 57.25, 120.3, 599.5, 599.999])
