@@ -129,7 +129,8 @@ typedef struct {
   double residual;   /* backward error of the coupled solve */
   double ion_energy_eV; /* energy of the ions absorbed at x = 0 in the push */
   double max_cfl;    /* max |u| (cells/step) in the push that produced level n */
-  double pad;
+  double J_hat;      /* learned weak scheme: predicted plasma charge used at this
+                        level (0 when the plain lagged solve was used) [C] */
   int64_t absorbed[2][3]; /* [x = 0, x = d][species] */
   int64_t emitted[2];     /* secondaries emitted at [x = 0, x = d] */
   int64_t injected;       /* beam ions appended */
@@ -166,9 +167,18 @@ int cp_set_particles(cp_ctx* ctx, int32_t species, const double* x, const double
 int cp_step_strict(cp_ctx* ctx, int32_t n_steps, double residual_tol);
 
 /* Advance n_steps steps with weak (one-step-lagged, operator-split)
-   coupling, Sec. 2.4.3: the free circuit gives Q*^n (load capacitor C), which
-   enters Eq. Poisson_BC3; afterwards Q^n := C phi_0^n.  Strict and weak calls
-   may be interleaved.  Errors as cp_step_strict. */
+   coupling, Sec. 2.4.3: the circuit alone is advanced first, its load
+   capacitor C starting from the electrode potential of the previous level
+   (the capacitor state handed back to the circuit, Q_4^{n-1} = C phi_0^{n-1})
+   while the circuit keeps its own loop-charge history:
+     a21 Q^n - hist + phi_0^{n-1} + (Q^n - Q^{n-1})/C = polarity V_s(t_n),
+   a21 and hist being the BDF2 terms of the strict scheme.  The capacitor
+   charge Q*^n = C phi_0^{n-1} + Q^n - Q^{n-1} then enters Eq. Poisson_BC3
+   (the circuit delivers Q^n - Q^{n-1} to the electrode).  Without plasma
+   this equals the strict solve; with plasma it lags the strict one by the
+   plasma's own change of C phi_0 over the step.  Q_circ in the diagnostics
+   is the loop charge Q^n in both schemes.  Strict and weak calls may be
+   interleaved.  Errors as cp_step_strict. */
 int cp_step_weak(cp_ctx* ctx, int32_t n_steps);
 
 /* Current level's diagnostics row (synchronises the stream). */
@@ -247,6 +257,110 @@ int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, double dt, u
                          int64_t step, int32_t half_kick, const double* E, float* xi, float* u,
                          const uint32_t* id, int64_t n, int64_t* G, float* se_xi, float* se_u,
                          int64_t se_cap, int64_t* counts, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned weak-coupling predictor.  The paper's weak scheme (Sec. 2.4.3)
+ * lags the strict one because its circuit solve sees the capacitor voltage
+ * phi_0^{n-1} + (Q^n - Q^{n-1})/C instead of phi_0^n; the difference is
+ * J^n/C with J^n = C (phi_0^n - phi_0^{n-1}) - (Q^n - Q^{n-1}), the
+ * plasma's own change of C phi_0 over the step (convection charge plus the
+ * change of the charge the space charge induces on the electrode).  A small
+ * MLP predicts J^n from the last 8 levels; the learned weak solve adds the
+ * prediction J_hat to its capacitor term,
+ *   a21 Q^n - hist + phi_0^{n-1} + (Q^n - Q^{n-1} + J_hat)/C = V_s,
+ * which is the strict solve when J_hat = J^n.
+ *
+ * Network: 40 -> 64 -> 64 -> 64 -> 2, GELU (erf form) after the three
+ * hidden layers, BF16 weights (rounded to nearest even from an FP32 master
+ * copy), FP32 biases, FP32 accumulation.  Parameters are one FP32 array of
+ * CP_MLP_NPARAM values: W1[64][40] b1[64] W2[64][64] b2[64] W3[64][64]
+ * b3[64] W4[2][64] b4[2] (W[out][in], row-major).
+ *
+ * Features of level k (raw, one row of 5): Q_conv^k [C], phi_0^k -
+ * phi_0^{k-1} [V], Q_surf^k - Q_surf^{k-1} [C], secondaries emitted at
+ * x = 0 in step k, energy of the ions absorbed at x = 0 in step k [eV].  The
+ * input predicting level n+1 is the rows of levels n-7..n (oldest first),
+ * each value divided by in_scale of its feature.  Outputs (y0, y1) are
+ * Q_conv^{n+1} / out_scale[0] and (J^{n+1} - Q_conv^{n+1}) / out_scale[1];
+ * J_hat = out_scale[0] y0 + out_scale[1] y1.
+ *
+ * Fallback: the network is evaluated at every level once 8 levels of
+ * features exist (in every scheme), and its error against the realised J^n
+ * is tracked as exponential averages (weight 1/16) of |J^n - J_hat^n| and
+ * |J^n|.  The learned solve uses J_hat only after 16 such evaluations and
+ * while avg|J - J_hat| <= bound * avg|J| (bound > 0); otherwise it falls
+ * back to the plain lagged solve (J_hat = 0) for that level.
+ * ------------------------------------------------------------------------ */
+#define CP_MLP_IN 40
+#define CP_MLP_HIDDEN 64
+#define CP_MLP_OUT 2
+#define CP_MLP_NPARAM 11074
+#define CP_PRED_WINDOW 8
+#define CP_PRED_FEATURES 5
+
+typedef struct {
+  float in_scale[5];  /* divisors of the five features (> 0) */
+  float out_scale[2]; /* multipliers of the two outputs (> 0) */
+  float pad0;
+  double bound;       /* fallback bound on avg|J - J_hat| / avg|J| (> 0) */
+} cp_predictor;
+
+/* Install a trained network in the context (params: host, CP_MLP_NPARAM
+   FP32 values; rounded to BF16 on the device).  From the next solve on, the
+   network is evaluated at every level and its error tracked; only
+   cp_step_weak_learned uses its predictions.  Errors: CP_ERR_ARG (null
+   pointers, scales <= 0 or not finite, bound <= 0), CP_ERR_CUDA. */
+int cp_set_predictor(cp_ctx* ctx, const float* params, const cp_predictor* norm);
+
+/* Advance n_steps steps with the learned weak scheme described above.
+   Errors: CP_ERR_ARG if no predictor is installed; otherwise as
+   cp_step_weak. */
+int cp_step_weak_learned(cp_ctx* ctx, int32_t n_steps);
+
+/* Training samples from the context's history rows: for k = 0..n-1 the
+   window ending at level L = first_level + k (raw features, not divided by
+   the scales) goes to X[k][0..39] and the targets of level L+1 to Y[k][0]
+   = Q_conv^{L+1}, Y[k][1] = J^{L+1} - Q_conv^{L+1} [C].  X (n x 40) and Y
+   (n x 2) are FP32 device arrays; values are formed in FP64 and rounded
+   once.  Requires first_level >= 8 and first_level + n <= the current level.
+   Stream-ordered on the context's stream.  Errors: CP_ERR_ARG. */
+int cp_predictor_samples(cp_ctx* ctx, int64_t first_level, int64_t n, float* X, float* Y);
+
+/* Training kernels.  All arrays are FP32 device arrays; work is issued on
+   `stream` (cudaStream_t, may be NULL).  No call allocates memory. */
+
+/* Initialise params (CP_MLP_NPARAM): weights uniform in +-sqrt(6/fan_in)
+   (He), biases 0, from Philox4x64-10 draws keyed by seed. */
+int cp_mlp_init(float* params, uint64_t seed, void* stream);
+
+/* Feature and target scales of a data set (X: n x 40 raw, Y: n x 2 raw):
+   in_scale[f] = root mean square of feature f over all samples and window
+   positions, out_scale[o] = RMS of Y[:, o] (1 where the RMS is 0).  Fills
+   the scales of *norm (bound untouched); synchronises the stream. */
+int cp_mlp_scales(const float* X, const float* Y, int64_t n, cp_predictor* norm, void* stream);
+
+/* Xn = X / in_scale, Yn = Y / out_scale (Y/Yn may be NULL). */
+int cp_mlp_normalize(const float* X, const float* Y, int64_t n, const cp_predictor* norm,
+                     float* Xn, float* Yn, void* stream);
+
+/* Network outputs (normalised) for n normalised inputs: Yhat (n x 2). */
+int cp_mlp_forward(const float* params, const float* Xn, int64_t n, float* Yhat, void* stream);
+
+/* Loss and gradient of L = 1/(2n) sum_k sum_o (yhat_ko - y_ko)^2 with
+   respect to params (the BF16-rounded weights are used in the forward and
+   backward passes; the gradient is taken with respect to them and applied
+   to the FP32 master copy).  grad: CP_MLP_NPARAM floats, *loss: one float
+   (device).  work: cp_mlp_work_floats() floats of scratch (device).
+   Deterministic: per-block partial sums are added in a fixed order. */
+int64_t cp_mlp_work_floats(void);
+int cp_mlp_loss_grad(const float* params, const float* Xn, const float* Yn, int64_t n,
+                     float* grad, float* loss, float* work, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) at step number t >= 1:
+   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+   p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */
+int cp_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t t, float lr,
+                float beta1, float beta2, float eps, void* stream);
 
 void cp_destroy(cp_ctx* ctx);
 const char* cp_status_str(int status);

@@ -30,6 +30,9 @@ cudaError_t solve_launch(int precision, const Bufs& B, int ctas, size_t smem, cu
 cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t st);
 cudaError_t fill_launch(int precision, void* p, int64_t n, double v, cudaStream_t st);
 cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st);
+cudaError_t pack_predictor_launch(const float* params, PredNet* net, cudaStream_t st);
+cudaError_t samples_launch(const DevParams* P, const cp_diag* hist, int64_t first, int64_t n,
+                           float* X, float* Y, cudaStream_t st);
 }  // namespace cpk
 
 using cpk::kSpecies;
@@ -70,8 +73,9 @@ struct cp_ctx {
   // particles staged on the host until the first step
   std::vector<double> hx[kSpecies], hu[kSpecies];
   std::vector<uint32_t> hid;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  double gtol[2] = {0.0, 0.0};
+  cpk::PredNet* net = nullptr;  // installed predictor network (device), or null
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // strict, weak, learned weak
+  double gtol[3] = {0.0, 0.0, 0.0};
   int64_t launches = 0;
   bool timing = false;
   double t_ms[3] = {0.0, 0.0, 0.0};  // push, solve, removal
@@ -106,6 +110,7 @@ cpk::Bufs make_bufs(const cp_ctx* c) {
   B.hist = c->hist;
   B.hist_rows = c->hist_rows;
   B.vs = c->vs;
+  B.net = c->net;
   return B;
 }
 
@@ -129,7 +134,8 @@ void free_all(cp_ctx* c) {
   cudaFree(c->vs);
   cudaFree(c->dP);
   cudaFree(c->dS);
-  for (int m = 0; m < 2; ++m)
+  cudaFree(c->net);
+  for (int m = 0; m < 3; ++m)
     if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -448,6 +454,7 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.alpha = dx * dx * P.scale / P.eps0;
   P.g_strict = P.a21 > 0 ? 1.0 / P.a21 : 0.0;
   P.g_weak = 1.0 / (P.a21 + 1.0 / P.C);
+  P.inv_C = P.C > 0 ? 1.0 / P.C : 0.0;
   P.gam_strict = P.g_strict * dx / (P.eps0 * P.area);
   P.inv_den_strict = 1.0 / (1.0 + static_cast<double>(P.N) * P.gam_strict);
   P.dx_eps0 = dx / P.eps0;
@@ -504,6 +511,59 @@ int cp_step_strict(cp_ctx* c, int32_t n_steps, double residual_tol) {
 }
 
 int cp_step_weak(cp_ctx* c, int32_t n_steps) { return do_steps(c, 1, n_steps, 1e300); }
+
+int cp_step_weak_learned(cp_ctx* c, int32_t n_steps) {
+  if (!c || !c->net) return CP_ERR_ARG;
+  return do_steps(c, 2, n_steps, 1e300);
+}
+
+int cp_set_predictor(cp_ctx* c, const float* params, const cp_predictor* norm) {
+  if (!c || !params || !norm) return CP_ERR_ARG;
+  for (int f = 0; f < CP_PRED_FEATURES; ++f)
+    if (!(norm->in_scale[f] > 0.0f) || !std::isfinite(norm->in_scale[f])) return CP_ERR_ARG;
+  for (int o = 0; o < CP_MLP_OUT; ++o)
+    if (!(norm->out_scale[o] > 0.0f) || !std::isfinite(norm->out_scale[o])) return CP_ERR_ARG;
+  if (!(norm->bound > 0.0) || !std::isfinite(norm->bound)) return CP_ERR_ARG;
+  for (int k = 0; k < CP_MLP_NPARAM; ++k)
+    if (!std::isfinite(params[k])) return CP_ERR_ARG;
+  CP_CUDA(cudaSetDevice(c->device));
+  if (!c->net) CP_TRY(alloc(reinterpret_cast<void**>(&c->net), sizeof(cpk::PredNet)));
+  float* dparams = nullptr;
+  CP_TRY(alloc(reinterpret_cast<void**>(&dparams), sizeof(float) * CP_MLP_NPARAM));
+  int rc = cuda_rc(cudaMemcpyAsync(dparams, params, sizeof(float) * CP_MLP_NPARAM,
+                                   cudaMemcpyHostToDevice, c->stream));
+  if (rc == CP_OK) rc = cuda_rc(cpk::pack_predictor_launch(dparams, c->net, c->stream));
+  // scales and bound go straight into the packed struct
+  if (rc == CP_OK)
+    rc = cuda_rc(cudaMemcpyAsync(c->net->in_scale, norm->in_scale, sizeof(norm->in_scale),
+                                 cudaMemcpyHostToDevice, c->stream));
+  if (rc == CP_OK)
+    rc = cuda_rc(cudaMemcpyAsync(c->net->out_scale, norm->out_scale, sizeof(norm->out_scale),
+                                 cudaMemcpyHostToDevice, c->stream));
+  if (rc == CP_OK)
+    rc = cuda_rc(cudaMemcpyAsync(&c->net->bound, &norm->bound, sizeof(double),
+                                 cudaMemcpyHostToDevice, c->stream));
+  if (rc == CP_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
+  cudaFree(dparams);
+  // graphs captured before carry the old buffer set: rebuild on next use
+  for (int m = 0; m < 3; ++m) {
+    if (c->gexec[m]) cudaGraphExecDestroy(c->gexec[m]);
+    c->gexec[m] = nullptr;
+  }
+  return rc;
+}
+
+int cp_predictor_samples(cp_ctx* c, int64_t first_level, int64_t n, float* X, float* Y) {
+  if (!c || !X || !Y || n < 0 || first_level < CP_PRED_WINDOW || !c->initialized) return CP_ERR_ARG;
+  int64_t level = 0;
+  CP_CUDA(cudaSetDevice(c->device));
+  CP_CUDA(cudaMemcpyAsync(&level, &c->dS->level, sizeof(level), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  if (first_level + n > level || first_level + n >= c->hist_rows) return CP_ERR_ARG;
+  if (n == 0) return CP_OK;
+  CP_CUDA(cpk::samples_launch(c->dP, c->hist, first_level, n, X, Y, c->stream));
+  return CP_OK;
+}
 
 int cp_read_scalars(cp_ctx* c, cp_diag* out) {
   if (!c || !out) return CP_ERR_ARG;

@@ -40,6 +40,15 @@ constexpr int kSolveThreads = 512;
 constexpr double kFix = 65536.0;       // fixed-point units per macroparticle charge
 constexpr uint64_t kTagSee = 0x5345ULL;
 constexpr uint64_t kTagBeam = 0x4245ULL;
+constexpr uint64_t kTagInit = 0x4D4C50ULL;  // MLP parameter initialisation draws
+// predictor network shape and feature window
+constexpr int kPredWindow = 8;
+constexpr int kPredFeat = 5;
+constexpr int kPredIn = kPredWindow * kPredFeat;  // 40
+constexpr int kHid = 64;
+constexpr int kPredOut = 2;
+constexpr int kPredMinEval = 16;  // checked predictions before the first use
+constexpr double kPredAvg = 1.0 / 16.0;  // weight of the running error averages
 
 struct DevParams {
   int32_t N;
@@ -59,6 +68,7 @@ struct DevParams {
   // host-precomputed factors so that the solve divides nothing in FP64
   double g_strict;       // 1 / a21
   double g_weak;         // 1 / (a21 + 1/C)
+  double inv_C;          // 1 / C
   double gam_strict;     // g_strict dx / (eps0 A)
   double inv_den_strict; // 1 / (1 + N gam_strict)
   double dx_eps0;        // dx / eps0
@@ -101,10 +111,31 @@ struct DevState {
   long long ion_energy_q;     // sum of rint(256 E_eV) over ions absorbed at x = 0
   unsigned int max_cfl_bits;  // float bits of max |u| (non-negative floats order as ints)
   double nxt_Vs, nxt_hist;     // source and BDF2 history of the next level
+  double phi0_last;           // phi_0 of the current level (weak: capacitor state)
+  // learned weak-coupling predictor (evaluated when a network is installed)
+  double feat[kPredWindow][kPredFeat];  // raw feature rows of the last 8 levels
+  int32_t n_feat;             // rows filled (saturates at kPredWindow)
+  int32_t pred_ready;         // J_pred holds a prediction for the next level
+  double J_pred;              // network's J_hat for the next level [C]
+  double err_avg, J_avg;      // running averages of |J - J_hat| and |J|
+  int64_t n_eval;             // predictions checked against the realised J
   unsigned long long compact_n[kSpecies];
   unsigned int compact_done;
   uint32_t beam_id_base;
   cp_diag cur;                // diagnostics of the current level
+};
+
+// Installed predictor network: BF16 weights (raw bits, W[out][in]), FP32
+// biases and scales.
+struct PredNet {
+  uint16_t W1[kHid * kPredIn];
+  uint16_t W2[kHid * kHid];
+  uint16_t W3[kHid * kHid];
+  uint16_t W4[kPredOut * kHid];
+  float b1[kHid], b2[kHid], b3[kHid], b4[kPredOut];
+  float in_scale[kPredFeat];
+  float out_scale[kPredOut];
+  double bound;
 };
 
 struct Bufs {
@@ -119,6 +150,7 @@ struct Bufs {
   cp_diag* hist;
   int64_t hist_rows;
   const double* vs;  // polarity V_s(t_n) for every level n (filled once at set-up)
+  const PredNet* net;  // installed predictor, or null
 };
 
 // ---------------------------------------------------------------------------

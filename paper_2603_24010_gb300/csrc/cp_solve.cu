@@ -11,6 +11,7 @@
 //   refinement if it exceeds the requested tolerance.  Chunk totals are
 //   exchanged through distributed shared memory.
 #include "cp_common.cuh"
+#include "cp_mlp.cuh"
 
 namespace cpk {
 // ---------------------------------------------------------------------------
@@ -267,6 +268,82 @@ __device__ void cta_max3(unsigned long long& a, unsigned long long& b, unsigned 
   }
 }
 
+// Circuit charge, surface charge and current of a solved level from the
+// circuit scalars of the solve (sc: [2] g, [3] K or Q^n, [6] Q_conv, [7]
+// sigma_{n-1}, [8] Q^{n-1}, [9] Q^{n-2}) and the level's phi_0.
+__device__ __forceinline__ void level_charges(const DevParams* P, const double* sc, bool strict_rlc,
+                                              double phi0, double* Qn, double* sigma_n, double* I) {
+  const double Qconv = sc[6], sigma_prev = sc[7], Q1 = sc[8], Q2 = sc[9];
+  if (strict_rlc) {
+    *Qn = sc[3] - sc[2] * phi0;                             // Eqs. Q4_phi_relation, K_def
+    *sigma_n = sigma_prev + (Qconv + *Qn - Q1) * P->inv_A;  // Eq. sigma_update
+    *I = (3.0 * *Qn - 4.0 * Q1 + Q2) * P->inv_2dt;
+  } else if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
+    *Qn = sc[3];                                            // weak: the circuit's loop charge
+    *sigma_n = sigma_prev + (Qconv + *Qn - Q1) * P->inv_A;  // Eq. top_plate_charge
+    *I = (3.0 * *Qn - 4.0 * Q1 + Q2) * P->inv_2dt;
+  } else {
+    *Qn = Q1;
+    *sigma_n = sigma_prev + Qconv * P->inv_A;
+    *I = 0.0;
+  }
+}
+
+// Predictor step on one CTA (all threads): append the feature row of the
+// level just solved to the 8-level window and, once the window is full,
+// evaluate the network for the next level's J_hat.
+__device__ __noinline__ void predictor_update(const Bufs& B, const double* sc, bool strict_rlc,
+                                              double phi0) {
+  const DevParams* P = B.P;
+  DevState* S = B.S;
+  const PredNet* net = B.net;
+  __shared__ float x[kPredIn];
+  __shared__ float h1[kHid], h2[kHid], h3[kHid];
+  __shared__ float y[kPredOut];
+  __shared__ int s_full;
+  if (threadIdx.x == 0) {
+    double Qn, sigma_n, I;
+    level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
+    const double A = P->area;
+    double row[kPredFeat];
+    row[0] = sc[6];                    // Q_conv^n
+    row[1] = phi0 - sc[32];            // phi_0^n - phi_0^{n-1}
+    row[2] = sigma_n * A - sc[7] * A;  // Q_surf^n - Q_surf^{n-1}
+    row[3] = sc[33];                   // secondaries emitted at x = 0
+    row[4] = sc[34];                   // energy of the ions absorbed at x = 0 [eV]
+    for (int j = 0; j + 1 < kPredWindow; ++j)
+      for (int f = 0; f < kPredFeat; ++f) S->feat[j][f] = S->feat[j + 1][f];
+    for (int f = 0; f < kPredFeat; ++f) S->feat[kPredWindow - 1][f] = row[f];
+    const int nf = min(S->n_feat + 1, kPredWindow);
+    S->n_feat = nf;
+    s_full = (nf == kPredWindow);
+  }
+  __syncthreads();
+  if (!s_full) {
+    if (threadIdx.x == 0) S->pred_ready = 0;
+    return;
+  }
+  if (threadIdx.x < kPredIn) {
+    const int f = threadIdx.x % kPredFeat;
+    x[threadIdx.x] = static_cast<float>(S->feat[threadIdx.x / kPredFeat][f] /
+                                        static_cast<double>(net->in_scale[f]));
+  }
+  __syncthreads();
+  dense_one<kPredIn, kHid, true>(net->W1, net->b1, x, h1);
+  __syncthreads();
+  dense_one<kHid, kHid, true>(net->W2, net->b2, h1, h2);
+  __syncthreads();
+  dense_one<kHid, kHid, true>(net->W3, net->b3, h2, h3);
+  __syncthreads();
+  dense_one<kHid, kPredOut, false>(net->W4, net->b4, h3, y);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S->J_pred = static_cast<double>(net->out_scale[0]) * static_cast<double>(y[0]) +
+                static_cast<double>(net->out_scale[1]) * static_cast<double>(y[1]);
+    S->pred_ready = 1;
+  }
+}
+
 template <typename real>
 __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push, int mode, double tol) {
   using real2 = typename Pair<real>::type;
@@ -287,7 +364,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
   __shared__ SolveSlotB slotB;
   __shared__ SolveSlotC slotC;
   __shared__ double slotd;
-  __shared__ double sc[32];
+  __shared__ double sc[40];
   __shared__ int s_stop;
 
   cudaGridDependencySynchronize();  // the push that deposited G has completed
@@ -407,6 +484,15 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
       const double Q4 = ldcg(&S->Qh[3]);
       hist = P->L4dt2 * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) + P->R2dt * (4.0 * Q1 - Q2);
     }
+    const double phi0_prev = ldcg(&S->phi0_last);
+    // learned weak scheme: the network's prediction of the plasma's change of
+    // C phi_0 over this step, used while its tracked error is within bound
+    const int pred_ready = (B.net != nullptr) ? ldcg(&S->pred_ready) : 0;
+    const double J_pred = pred_ready ? ldcg(&S->J_pred) : 0.0;
+    double J_used = 0.0;
+    if (mode == 2 && pred_ready && ldcg(&S->n_eval) >= kPredMinEval &&
+        ldcg(&S->err_avg) <= B.net->bound * ldcg(&S->J_avg))
+      J_used = J_pred;
     double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
     if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
       if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
@@ -414,8 +500,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
         Qpart = g * (Vs + hist);
         gam = P->gam_strict;
         inv_den = P->inv_den_strict;
-      } else {  // weak: free circuit with its load capacitor gives Q*^n
-        Qpart = (Vs + hist) * P->g_weak;
+      } else {
+        // weak (Sec. 2.4.3): the circuit alone, its load capacitor starting
+        // from phi_0^{n-1}: a21 Q - hist + phi_0^{n-1} + (Q - Q^{n-1} + J)/C = V_s
+        Qpart = (Vs + hist + (Q1 - J_used) * P->inv_C - phi0_prev) * P->g_weak;
       }
     }
     const double Qconv = static_cast<double>(conv) * qw;
@@ -431,6 +519,17 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     const double D0 = b0 - gam * phi0;  // D_0 = x_0 - x_1
     sc[11] = D0;
     sc[12] = static_cast<double>(conv);
+    sc[15] = J_used;
+    sc[30] = J_pred;
+    sc[31] = static_cast<double>(pred_ready);
+    sc[32] = phi0_prev;
+    if (do_push) {  // the push's tallies, read before the commit clears them
+      sc[33] = static_cast<double>(ldcg(&S->emitted[0]));
+      sc[34] = static_cast<double>(ldcg(&S->ion_energy_q)) / 256.0;
+    } else {
+      sc[33] = 0.0;
+      sc[34] = 0.0;
+    }
     sc[24] = D0 * P->inv_dx;        // E_0
     sc[25] = P->alpha * P->inv_dx;  // dE_i / dS'_i
   }
@@ -476,6 +575,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     phi0 = sc[29];
   }
   double eta = 0.0;
+  double phi0_fin = phi0;  // x_0 after any refinement
   cg::cluster_group::arrival_token done_tok;
   for (int sweep = 0; sweep <= 3; ++sweep) {
     unsigned long long rm = 0ULL, xm = 0ULL, bm = 0ULL;
@@ -574,6 +674,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     cl.sync();
     nextE = (hi < N) ? cl.map_shared_rank(&slotB, rank + 1)->first_E : 0.0;
     sc[13] = phi0_new;
+    phi0_fin = phi0_new;
   }
 
   // outputs; the gather table pairs need the next chunk's first field value
@@ -599,28 +700,20 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
   // barrier D: no rank leaves (freeing its shared memory) before every
   // rank's remote reads are done
   cl.barrier_wait(std::move(done_tok));
+  if (rank == 1) {
+    if (B.net != nullptr && do_push) predictor_update(B, sc, strict_rlc, phi0_fin);
+    return;
+  }
   if (rank != 0) return;
 
   if (threadIdx.x == 0) {
     const int64_t level = S->level + (do_push ? 1 : 0);
     const double dt = P->dt, A = P->area;
     const double phi0 = ph[0];
-    const double Qconv = sc[6], sigma_prev = sc[7], Q1 = sc[8], Q2 = sc[9], Q3 = sc[10];
+    const double Qconv = sc[6], Q1 = sc[8], Q2 = sc[9], Q3 = sc[10];
     const long long conv = static_cast<long long>(sc[12]);
     double Qn, sigma_n, I;
-    if (strict_rlc) {
-      Qn = sc[3] - sc[2] * phi0;
-      sigma_n = sigma_prev + (Qconv + Qn - Q1) * P->inv_A;  // Eq. sigma_update
-      I = (3.0 * Qn - 4.0 * Q1 + Q2) * P->inv_2dt;
-    } else if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
-      sigma_n = sigma_prev + (Qconv + sc[3] - Q1) * P->inv_A;  // Eq. top_plate_charge with Q*^n
-      Qn = P->C * phi0;                                        // weak overwrite Q^n := C phi_0^n
-      I = (3.0 * sc[3] - 4.0 * Q1 + Q2) * P->inv_2dt;
-    } else {
-      sigma_n = sigma_prev + Qconv * P->inv_A;
-      Qn = Q1;
-      I = 0.0;
-    }
+    level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
     int status = 0;
     if (!isfinite(phi0) || !isfinite(sigma_n) || !isfinite(Qn)) status = CP_ERR_NONFINITE;
     else if (eta > tol) status = CP_ERR_RESIDUAL;
@@ -634,11 +727,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     d.Q_conv = Qconv;
     d.Q_circ = Qn;
     d.V_source = sc[4];
-    (void)A;
     d.residual = eta;
     d.ion_energy_eV = do_push ? static_cast<double>(S->ion_energy_q) / 256.0 : 0.0;
     d.max_cfl = do_push ? static_cast<double>(__uint_as_float(S->max_cfl_bits)) : 0.0;
-    d.pad = 0.0;
+    d.J_hat = sc[15];
     long long nl[kSpecies];
     for (int s = 0; s < kSpecies; ++s) {
       for (int e = 0; e < 2; ++e)
@@ -655,8 +747,17 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     S->cur = d;
     if (level < B.hist_rows) B.hist[level] = d;
 
+    // the network's prediction for this level against the realised
+    // J^n = C (phi_0^n - phi_0^{n-1}) - (Q^n - Q^{n-1})
+    if (sc[31] != 0.0) {
+      const double J = P->C * (phi0 - sc[32]) - (Qn - Q1);
+      S->err_avg += (fabs(J - sc[30]) - S->err_avg) * kPredAvg;
+      S->J_avg += (fabs(J) - S->J_avg) * kPredAvg;
+      S->n_eval += 1;
+    }
     // commit the circuit and surface-charge state of the new level
     S->sigma = sigma_n;
+    S->phi0_last = phi0;
     S->Qh[3] = Q3;
     S->Qh[2] = Q2;
     S->Qh[1] = Q1;

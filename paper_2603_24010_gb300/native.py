@@ -24,8 +24,13 @@ UNITS_CELL, UNITS_SI = 0, 1
 EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "cp_read_scalars",
            "cp_read_history", "cp_read_grid", "cp_get_particles", "cp_get_level",
            "cp_save_state", "cp_load_state", "cp_last_launch_count", "cp_enable_timing",
-           "cp_read_timing", "cp_read_launch_times", "cp_push_ions_noalloc", "cp_destroy",
-           "cp_status_str")
+           "cp_read_timing", "cp_read_launch_times", "cp_push_ions_noalloc", "cp_set_predictor",
+           "cp_step_weak_learned", "cp_predictor_samples", "cp_mlp_init", "cp_mlp_scales",
+           "cp_mlp_normalize", "cp_mlp_forward", "cp_mlp_work_floats", "cp_mlp_loss_grad",
+           "cp_mlp_adam", "cp_destroy", "cp_status_str")
+STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 40, 64, 2, 11074
+PRED_WINDOW, PRED_FEATURES = 8, 5
 
 
 class CpError(RuntimeError):
@@ -59,9 +64,14 @@ class cp_run(C.Structure):
 class cp_diag(C.Structure):
     _fields_ = [("step", C.c_int64)] + [(n, C.c_double) for n in (
         "t", "V_gap", "I_circ", "Q_surf", "Q_conv", "Q_circ", "V_source", "residual",
-        "ion_energy_eV", "max_cfl", "pad")] + [
+        "ion_energy_eV", "max_cfl", "J_hat")] + [
         ("absorbed", (C.c_int64 * 3) * 2), ("emitted", C.c_int64 * 2), ("injected", C.c_int64),
         ("n_live", C.c_int64 * 3), ("conv_count", C.c_int64)]
+
+
+class cp_predictor(C.Structure):
+    _fields_ = [("in_scale", C.c_float * 5), ("out_scale", C.c_float * 2), ("pad0", C.c_float),
+                ("bound", C.c_double)]
 
 
 _lib = None
@@ -94,6 +104,19 @@ def lib():
         L.cp_push_ions_noalloc.argtypes = [C.POINTER(cp_gap), C.POINTER(cp_see_beam), C.c_double,
                                            C.c_uint64, C.c_int64, C.c_int32, vp, vp, vp, vp,
                                            C.c_int64, vp, vp, vp, C.c_int64, vp, vp]
+        fp = C.c_void_p  # device float arrays are passed as addresses
+        L.cp_set_predictor.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(cp_predictor)]
+        L.cp_step_weak_learned.argtypes = [vp, C.c_int32]
+        L.cp_predictor_samples.argtypes = [vp, C.c_int64, C.c_int64, fp, fp]
+        L.cp_mlp_init.argtypes = [fp, C.c_uint64, vp]
+        L.cp_mlp_scales.argtypes = [fp, fp, C.c_int64, C.POINTER(cp_predictor), vp]
+        L.cp_mlp_normalize.argtypes = [fp, fp, C.c_int64, C.POINTER(cp_predictor), fp, fp, vp]
+        L.cp_mlp_forward.argtypes = [fp, fp, C.c_int64, fp, vp]
+        L.cp_mlp_work_floats.argtypes = []
+        L.cp_mlp_work_floats.restype = C.c_int64
+        L.cp_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, vp]
+        L.cp_mlp_adam.argtypes = [fp, fp, fp, fp, C.c_int64, C.c_float, C.c_float, C.c_float,
+                                  C.c_float, vp]
         L.cp_destroy.argtypes = [vp]
         L.cp_destroy.restype = None
         L.cp_status_str.argtypes = [C.c_int]
@@ -243,6 +266,52 @@ def cp_push_ions_noalloc(gap, see, dt, seed, step, half_kick, E, xi, u, ids, n, 
                                       int(se_cap), counts, C.c_void_p(stream or 0))
 
 
+def cp_set_predictor(ctx, params, norm):
+    """params: host FP32 array of MLP_NPARAM values; norm: cp_predictor."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != MLP_NPARAM:
+        raise ValueError("expected %d parameters" % MLP_NPARAM)
+    return lib().cp_set_predictor(ctx, p.ctypes.data_as(C.POINTER(C.c_float)), C.byref(norm))
+
+
+def cp_step_weak_learned(ctx, n_steps):
+    return lib().cp_step_weak_learned(ctx, int(n_steps))
+
+
+def cp_predictor_samples(ctx, first_level, n, X, Y):
+    """X, Y: device addresses (int) of n x 40 and n x 2 FP32 arrays."""
+    return lib().cp_predictor_samples(ctx, int(first_level), int(n), X, Y)
+
+
+def cp_mlp_init(params, seed, stream=None):
+    return lib().cp_mlp_init(params, int(seed), C.c_void_p(stream or 0))
+
+
+def cp_mlp_scales(X, Y, n, norm, stream=None):
+    return lib().cp_mlp_scales(X, Y, int(n), C.byref(norm), C.c_void_p(stream or 0))
+
+
+def cp_mlp_normalize(X, Y, n, norm, Xn, Yn, stream=None):
+    return lib().cp_mlp_normalize(X, Y, int(n), C.byref(norm), Xn, Yn, C.c_void_p(stream or 0))
+
+
+def cp_mlp_forward(params, Xn, n, Yhat, stream=None):
+    return lib().cp_mlp_forward(params, Xn, int(n), Yhat, C.c_void_p(stream or 0))
+
+
+def cp_mlp_work_floats():
+    return int(lib().cp_mlp_work_floats())
+
+
+def cp_mlp_loss_grad(params, Xn, Yn, n, grad, loss, work, stream=None):
+    return lib().cp_mlp_loss_grad(params, Xn, Yn, int(n), grad, loss, work, C.c_void_p(stream or 0))
+
+
+def cp_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    return lib().cp_mlp_adam(params, grad, m, v, int(t), float(lr), float(beta1), float(beta2),
+                             float(eps), C.c_void_p(stream or 0))
+
+
 def cp_destroy(ctx):
     lib().cp_destroy(ctx)
 
@@ -297,8 +366,17 @@ class Gap:
         _check("cp_set_particles", cp_set_particles(self.ctx, species, xi, u, ids, units))
 
     def step(self, mode, n_steps, tol=1e-12):
-        rc = cp_step_strict(self.ctx, n_steps, tol) if mode == 0 else cp_step_weak(self.ctx, n_steps)
-        _check("cp_step_%s" % ("strict" if mode == 0 else "weak"), rc)
+        if mode == STRICT:
+            _check("cp_step_strict", cp_step_strict(self.ctx, n_steps, tol))
+        elif mode == WEAK:
+            _check("cp_step_weak", cp_step_weak(self.ctx, n_steps))
+        elif mode == WEAK_LEARNED:
+            _check("cp_step_weak_learned", cp_step_weak_learned(self.ctx, n_steps))
+        else:
+            raise ValueError("unknown coupling mode %r" % (mode,))
+
+    def set_predictor(self, params, norm):
+        _check("cp_set_predictor", cp_set_predictor(self.ctx, params, norm))
 
     @property
     def level(self):
@@ -324,8 +402,6 @@ def diag_to_dict(arr):
     out = {}
     n = len(arr)
     for name, typ in cp_diag._fields_:
-        if name == "pad":
-            continue
         if name == "absorbed":
             out[name] = np.array([[[arr[k].absorbed[e][s] for s in range(3)] for e in range(2)]
                                   for k in range(n)], dtype=np.int64).reshape(n, 2, 3)

@@ -16,6 +16,9 @@ injection profile are not available, so these parameter sets stand in):
 * ``gap_1d_fp32_large``: same gap with 4096 cells, 1e7 macroparticles (5e6
   pairs), 5000 beam macroparticles/step (mono 20 keV or uniform 5-50 keV
   depending on the seed), dt = 0.5 ps, 20000 steps; FP32 particles.
+* ``gap_1d_fp32_thinned``: the same physics with `factor` times fewer
+  macroparticles of `factor` times the weight (loaded pairs and beam alike):
+  the predictor's training and evaluation runs.
 """
 import math
 
@@ -59,6 +62,15 @@ def gap_1d_fp32_large(seed=0):
     rng = np.random.default_rng([seed, 0xBEA])
     cfg["beam_mode"] = int(rng.integers(0, 2))  # mono-energetic or uniform 5-50 keV
     cfg["name"] = "gap_1d_fp32_large"
+    return cfg
+
+
+def gap_1d_fp32_thinned(seed=0, factor=25, steps=20000):
+    """The large FP32 gap's distribution with factor x fewer, heavier macroparticles."""
+    cfg = _base(4096, 5_000_000 // factor, 0.5e-12, steps, 5000 // factor, FP32, seed)
+    rng = np.random.default_rng([seed, 0xBEA])
+    cfg["beam_mode"] = int(rng.integers(0, 2))
+    cfg["name"] = "gap_1d_fp32_thinned"
     return cfg
 
 

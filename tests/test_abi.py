@@ -58,8 +58,9 @@ def test_struct_layouts_match_c(tmp_path):
         "cp_circuit": ["R", "polarity", "kind"],
         "cp_see_beam": ["gamma_coef", "beam_Emax_eV", "beam_per_step", "beam_mode"],
         "cp_run": ["dt", "seed", "capacity", "max_steps", "precision", "compact_every"],
-        "cp_diag": ["step", "V_gap", "max_cfl", "absorbed", "emitted", "injected", "n_live",
-                    "conv_count"],
+        "cp_diag": ["step", "V_gap", "max_cfl", "J_hat", "absorbed", "emitted", "injected",
+                    "n_live", "conv_count"],
+        "cp_predictor": ["in_scale", "out_scale", "bound"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cp.h"', "int main(void){"]
     for s, fs in fields.items():
