@@ -9,6 +9,11 @@ that step / timed seconds.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
+After the timed run (outside it), the learned weak-coupling predictor is
+trained on strict runs of the same gap distribution and the V_gap(t) error of
+plain and learned weak coupling against strict is reported on held-out seeds
+("coupling"; skip with --no-coupling).
+
 ``--impl reference`` times the FP64 CPU oracle (the reference implementation
 of this build, written from the paper) on the host cores on a bounded sample
 of the same workload.
@@ -269,6 +274,57 @@ def run_native(args, rank, world):
                 clocks=clk, bpp=bpp, n_sel=n_sel, traffic=traffic, frac_psteps_above_l2=float(live[state > 129e6].sum()) / max(psteps, 1))
 
 
+# ---------------------------------------------------------------- coupling
+def run_coupling(args):
+    """The learned weak-coupling predictor on the large gap's distribution:
+    train on strict runs, then on held-out seeds compare the V_gap(t) error of
+    plain and learned weak coupling against strict, and the wall time of the
+    three schemes."""
+    import torch
+    from paper_2603_24010_gb300 import native
+    from paper_2603_24010_gb300 import predictor as PR
+    S, f = args.coupling_steps, args.coupling_factor
+    fam = lambda seed: W.gap_1d_fp32_thinned(seed, factor=f, steps=S)  # noqa: E731
+    t0 = time.perf_counter()
+    Xs, Ys = zip(*(PR.strict_samples(fam(1000 + k)) for k in range(args.coupling_train)))
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params, norm, losses = PR.train(X, Y, iters=args.coupling_iters, batch=8192, seed=1)
+    t_train = time.perf_counter() - t0
+    errs = {native.WEAK: [], native.WEAK_LEARNED: []}
+    ms = {native.STRICT: [], native.WEAK: [], native.WEAK_LEARNED: []}
+    used = []
+    for k in range(args.coupling_eval):
+        res = PR.evaluate(fam(2000 + k), params, norm)
+        e = PR.vgap_errors(res)
+        for m in errs:
+            errs[m].append(e[m])
+        for m in ms:
+            ms[m].append(res[m]["ms_per_step"])
+        used.append(float((res[native.WEAK_LEARNED]["J_hat"] != 0).mean()))
+    cfg = fam(2000)
+    return {
+        "workload": ("gap_1d_fp32_thinned: the large gap's distribution (4096 cells, seed-drawn "
+                     "beam mode) with %d x fewer, heavier macroparticles: %d pairs, %d beam "
+                     "ions/step, dt %.3g s, %d steps" % (f, cfg["n_pairs"], cfg["beam_per_step"],
+                                                         cfg["dt"], S)),
+        "train_runs": args.coupling_train, "eval_runs": args.coupling_eval,
+        "samples": int(X.shape[0]), "train_iters": args.coupling_iters,
+        "loss_first_last": [losses[0], losses[-1]],
+        "metric": "max_t |V_gap - V_gap(strict)| / max_t |V_gap(strict)|, mean over eval seeds",
+        "vgap_err_weak": float(np.mean(errs[native.WEAK])),
+        "vgap_err_learned": float(np.mean(errs[native.WEAK_LEARNED])),
+        "vgap_err_weak_per_seed": errs[native.WEAK],
+        "vgap_err_learned_per_seed": errs[native.WEAK_LEARNED],
+        "predictor_used_frac": float(np.mean(used)),
+        "ms_per_step": {"strict": float(np.mean(ms[native.STRICT])),
+                        "weak": float(np.mean(ms[native.WEAK])),
+                        "weak_learned": float(np.mean(ms[native.WEAK_LEARNED]))},
+        "seconds": {"data": t_data, "train": t_train},
+    }
+
+
 # ---------------------------------------------------------------- oracle arm
 def oracle_sample(cfg, K, Wm, budget_s, rate_guess=4e7):
     """Run the FP64 oracle on a sub-sampled copy of the workload (fewer
@@ -314,6 +370,13 @@ def main():
                     help="override the workload's loaded pairs (weight scaled to keep the density)")
     ap.add_argument("--single", action="store_true",
                     help="only the device-resident graph pass (for profiler captures)")
+    ap.add_argument("--no-coupling", action="store_true",
+                    help="skip the learned-vs-plain weak coupling comparison")
+    ap.add_argument("--coupling-train", type=int, default=16)
+    ap.add_argument("--coupling-eval", type=int, default=4)
+    ap.add_argument("--coupling-steps", type=int, default=20000)
+    ap.add_argument("--coupling-factor", type=int, default=25)
+    ap.add_argument("--coupling-iters", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -361,6 +424,7 @@ def main():
         v, desc = oracle_sample(cfg, 200, 3, budget_s=20.0)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                "sample": desc}
+    coupling = None if args.no_coupling else run_coupling(args)
     K = args.steps
     value = r["psteps"] / (r["ms"] * 1e-3)
     line = {
@@ -383,6 +447,7 @@ def main():
                      "source": "per-launch CUDA events in a second pass over the same steps"},
         "clocks": r["clocks"],
         "cpu_baseline": cpu,
+        "coupling": coupling,
         "particle_steps": r["psteps"],
         "frac_particle_steps_state_above_l2": r["frac_psteps_above_l2"],
     }

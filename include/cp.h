@@ -281,8 +281,9 @@ int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, double dt, u
  * x = 0 in step k, energy of the ions absorbed at x = 0 in step k [eV].  The
  * input predicting level n+1 is the rows of levels n-7..n (oldest first),
  * each value divided by in_scale of its feature.  Outputs (y0, y1) are
- * Q_conv^{n+1} / out_scale[0] and (J^{n+1} - Q_conv^{n+1}) / out_scale[1];
- * J_hat = out_scale[0] y0 + out_scale[1] y1.
+ * Q_conv^{n+1} / out_scale[0] (the next step's plasma current times dt) and
+ * J^{n+1} / out_scale[1] (the plasma-driven increment of the electrode's
+ * charge); J_hat = out_scale[1] y1, y0 being an auxiliary output.
  *
  * Fallback: the network is evaluated at every level once 8 levels of
  * features exist (in every scheme), and its error against the realised J^n
@@ -320,7 +321,7 @@ int cp_step_weak_learned(cp_ctx* ctx, int32_t n_steps);
 /* Training samples from the context's history rows: for k = 0..n-1 the
    window ending at level L = first_level + k (raw features, not divided by
    the scales) goes to X[k][0..39] and the targets of level L+1 to Y[k][0]
-   = Q_conv^{L+1}, Y[k][1] = J^{L+1} - Q_conv^{L+1} [C].  X (n x 40) and Y
+   = Q_conv^{L+1}, Y[k][1] = J^{L+1} [C].  X (n x 40) and Y
    (n x 2) are FP32 device arrays; values are formed in FP64 and rounded
    once.  Requires first_level >= 8 and first_level + n <= the current level.
    Stream-ordered on the context's stream.  Errors: CP_ERR_ARG. */

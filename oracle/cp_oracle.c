@@ -497,7 +497,7 @@ static int solve_level(or_state* s, int32_t mode, double tol, int64_t conv_count
         for (int j = 0; j < 8; ++j)
           for (int f = 0; f < 5; ++f) x[5 * j + f] = s->feat[j][f] / s->in_scale[f];
         or_mlp_forward(s->pred_params, 1, x, y);
-        s->J_pred = s->out_scale[0] * y[0] + s->out_scale[1] * y[1];
+        s->J_pred = s->out_scale[1] * y[1]; /* y[0], the next Q_conv, is auxiliary */
         s->pred_ready = 1;
       }
     }

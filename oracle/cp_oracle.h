@@ -142,8 +142,8 @@ int or_solve_fields(const or_params* p, int32_t mode, const int64_t* G, int64_t 
    40-64-64-64-2 GELU network with bfloat16 weights predicts it from the
    last 8 levels' features (Q_conv, phi_0 increment, Q_surf increment,
    secondaries emitted at x = 0, absorbed ion energy at x = 0), each divided
-   by in_scale of its feature; outputs are Q_conv^{n+1}/out_scale[0] and
-   (J^{n+1} - Q_conv^{n+1})/out_scale[1].  The learned weak mode uses the
+   by in_scale of its feature; outputs are Q_conv^{n+1}/out_scale[0]
+   (auxiliary) and J^{n+1}/out_scale[1], so J_hat = out_scale[1] y[1].  The learned weak mode uses the
    prediction once 16 predictions have been checked against the realised J
    and while the running average (weight 1/16) of |J - J_hat| is at most
    bound times that of |J|; otherwise the plain lagged solve. */

@@ -86,7 +86,7 @@ __global__ void k_samples(const DevParams* __restrict__ P, const cp_diag* __rest
   const cp_diag& b = h[L];
   const double J = P->C * (a.V_gap - b.V_gap) - (a.Q_circ - b.Q_circ);
   Y[2 * k + 0] = static_cast<float>(a.Q_conv);
-  Y[2 * k + 1] = static_cast<float>(J - a.Q_conv);
+  Y[2 * k + 1] = static_cast<float>(J);
 }
 
 // ---------------------------------------------------------------------------

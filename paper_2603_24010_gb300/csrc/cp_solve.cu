@@ -338,8 +338,7 @@ __device__ __noinline__ void predictor_update(const Bufs& B, const double* sc, b
   dense_one<kHid, kPredOut, false>(net->W4, net->b4, h3, y);
   __syncthreads();
   if (threadIdx.x == 0) {
-    S->J_pred = static_cast<double>(net->out_scale[0]) * static_cast<double>(y[0]) +
-                static_cast<double>(net->out_scale[1]) * static_cast<double>(y[1]);
+    S->J_pred = static_cast<double>(net->out_scale[1]) * static_cast<double>(y[1]);
     S->pred_ready = 1;
   }
 }

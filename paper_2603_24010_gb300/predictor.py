@@ -93,7 +93,7 @@ def train(X, Y, iters=3000, batch=8192, lr=2e-3, lr_final=1e-4, seed=0, bound=0.
         native._check("cp_mlp_adam", native.cp_mlp_adam(params.data_ptr(), grad.data_ptr(),
                                                         m.data_ptr(), v.data_ptr(), it, rate,
                                                         stream=st))
-        if it % 100 == 0 or it == iters:
+        if it == 1 or it % 100 == 0 or it == iters:
             losses.append(float(loss.item()))
     torch.cuda.synchronize()
     return params.cpu().numpy(), norm, losses
