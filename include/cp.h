@@ -363,6 +363,61 @@ int cp_mlp_loss_grad(const float* params, const float* Xn, const float* Yn, int6
 int cp_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t t, float lr,
                 float beta1, float beta2, float eps, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Ensemble of independent gap instances (uneven cells and particle counts,
+ * their own circuits, SEE scales and beams) advanced together: per step one
+ * persistent push launch over the particle tiles of every instance and one
+ * solve launch with one CTA per instance, replayed from a CUDA graph.  An
+ * instance advanced in the ensemble gives bit for bit the results it gives
+ * as a context of its own (same per-particle arithmetic, integer charge,
+ * counter-based draws, exact integer solve).
+ * ------------------------------------------------------------------------ */
+typedef struct cp_batch cp_batch;
+
+/* Create n instances (1 <= n <= 2048) from arrays of n parameter structs.
+   All runs share precision, max_steps and compact_every; n_cells <= 4096.
+   Errors: CP_ERR_ARG, CP_ERR_OOM, CP_ERR_CUDA, and those of cp_create. */
+int cp_batch_create(int32_t n, const cp_gap* gaps, const cp_circuit* circuits,
+                    const cp_see_beam* sees, const cp_run* runs, void* stream, cp_batch** out);
+
+/* As cp_set_particles for instance i, before the first step. */
+int cp_batch_set_particles(cp_batch* b, int32_t i, int32_t species, const double* x,
+                           const double* v, const uint32_t* id, int64_t n, int32_t units);
+
+/* Advance every instance n_steps steps (strict / weak coupling as in
+   cp_step_strict / cp_step_weak).  An instance that meets an error stops
+   (the others go on); the call returns the first non-zero instance status,
+   cp_batch_status gives all of them. */
+int cp_batch_step_strict(cp_batch* b, int32_t n_steps, double residual_tol);
+int cp_batch_step_weak(cp_batch* b, int32_t n_steps);
+
+/* Per-instance readers, as their single-context counterparts. */
+int cp_batch_read_history(cp_batch* b, int32_t i, int64_t first, int64_t n, cp_diag* out);
+int cp_batch_read_grid(cp_batch* b, int32_t i, double* phi, double* rho, double* E, int64_t* G,
+                       int32_t n_nodes);
+int cp_batch_get_particles(cp_batch* b, int32_t i, int32_t species, double* xi, double* u,
+                           uint32_t* id, int64_t cap, int64_t* n);
+int cp_batch_status(cp_batch* b, int32_t* status /* n entries */);
+int cp_batch_get_level(cp_batch* b, int32_t i, int64_t* level);
+int cp_batch_last_launch_count(cp_batch* b, int64_t* launches);
+
+/* Launch shape of the ensemble push: threads per CTA (256, 512 or 1024) and
+   CTAs per SM (0 = as many as fit).  Valid after the first step.
+   Errors: CP_ERR_ARG if the shape cannot be resident. */
+int cp_batch_set_launch(cp_batch* b, int32_t threads, int32_t ctas_per_sm);
+int cp_batch_get_launch(cp_batch* b, int32_t* threads, int32_t* grid);
+
+/* Autotuner: for each candidate shape (512x2, 512x1, 256x2, 256x1, 1024x1
+   threads x CTAs per SM, those that fit) advance steps_per_shape ordinary
+   steps of the run (mode 0 strict with residual_tol, 1 weak), time the
+   push of each with CUDA events, and keep the fastest shape.  The steps
+   count as steps of the run (results do not depend on the shape).  Outputs
+   may be NULL.  Returns the first instance status. */
+int cp_batch_autotune(cp_batch* b, int32_t steps_per_shape, int32_t mode, double residual_tol,
+                      int32_t* threads, int32_t* ctas_per_sm, double* push_ms);
+
+void cp_batch_destroy(cp_batch* b);
+
 void cp_destroy(cp_ctx* ctx);
 const char* cp_status_str(int status);
 

@@ -31,6 +31,17 @@ cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t 
 cudaError_t fill_launch(int precision, void* p, int64_t n, double v, cudaStream_t st);
 cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st);
 cudaError_t pack_predictor_launch(const float* params, PredNet* net, cudaStream_t st);
+size_t push_ens_smem_bytes(int n_max, int precision, int E);
+int ens_max_instances();
+size_t abs_rec_ens_bytes();
+cudaError_t push_ens_occupancy(int precision, int threads, size_t smem, int* per_sm);
+cudaError_t push_ens_launch(int precision, int threads, int grid, size_t smem, const Bufs* Ball,
+                            int E, int n_max, void* abs, int abs_cap, cudaStream_t st);
+cudaError_t compact_ens_launch(int precision, const Bufs* Ball, int E, int grid, cudaStream_t st);
+cudaError_t solve_ens_configure(int precision, size_t smem);
+cudaError_t solve_ens_launch(int precision, const Bufs* Ball, int n_inst, size_t smem,
+                             cudaStream_t st, int do_push, int mode, double tol);
+cudaError_t status_ens_launch(const Bufs* Ball, int E, int* out, cudaStream_t st);
 cudaError_t samples_launch(const DevParams* P, const cp_diag* hist, int64_t first, int64_t n,
                            float* X, float* Y, cudaStream_t st);
 }  // namespace cpk
@@ -70,6 +81,7 @@ struct cp_ctx {
   int since_compact = 0;
   int64_t max_steps = 0;
   double sigma0 = 0.0;
+  bool ens_member = false;  // advanced by a cp_batch (its own absorbed-ion lists unused)
   // particles staged on the host until the first step
   std::vector<double> hx[kSpecies], hu[kSpecies];
   std::vector<uint32_t> hid;
@@ -225,7 +237,8 @@ int initialize(cp_ctx* c, int mode, double tol) {
   c->grid = per_sm * sms;
   c->hp.abs_cap = 4096;
   CP_TRY(alloc(reinterpret_cast<void**>(&c->abs),
-               sizeof(cpk::AbsRec) * static_cast<size_t>(c->grid) * c->hp.abs_cap));
+               sizeof(cpk::AbsRec) * (c->ens_member ? size_t(1)
+                                                    : static_cast<size_t>(c->grid) * c->hp.abs_cap)));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->dP), sizeof(cpk::DevParams)));
   CP_CUDA(cudaMemcpyAsync(c->dP, &c->hp, sizeof(cpk::DevParams), cudaMemcpyHostToDevice, c->stream));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->vs), sizeof(double) * (c->hist_rows + 1)));
@@ -834,6 +847,362 @@ const char* cp_status_str(int s) {
     case CP_ERR_TIMEOUT: return "bounded device wait gave up";
     default: return "unknown status";
   }
+}
+
+// ---- ensemble of independent instances ----------------------------------------
+}  // extern "C"
+
+struct cp_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<cp_ctx*> inst;
+  int E = 0;
+  int precision = CP_FP32;
+  int n_max = 0;
+  bool initialized = false;
+  cpk::Bufs* dBall = nullptr;
+  void* abs = nullptr;
+  int abs_cap = 4096;
+  int abs_grid = 0;      // CTAs the absorbed-ion lists were sized for
+  int push_threads = 512;
+  int push_grid = 0;
+  size_t push_smem = 0;
+  size_t solve_smem = 0;
+  int compact_grid = 0;
+  int compact_every = 64;
+  int since_compact = 0;
+  int64_t max_steps = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  double gtol[2] = {0.0, 0.0};
+  int64_t launches = 0;
+  int* dstatus = nullptr;
+};
+
+namespace {
+
+void batch_free(cp_batch* b) {
+  for (int m = 0; m < 2; ++m)
+    if (b->gexec[m]) cudaGraphExecDestroy(b->gexec[m]);
+  cudaFree(b->dBall);
+  cudaFree(b->abs);
+  cudaFree(b->dstatus);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cp_ctx* c : b->inst) cp_destroy(c);
+  b->inst.clear();
+}
+
+// Size the ensemble push for a block shape (threads, CTAs per SM <= occupancy).
+int batch_set_shape(cp_batch* b, int threads, int per_sm_req) {
+  if (threads != 256 && threads != 512 && threads != 1024) return CP_ERR_ARG;
+  int per_sm = 0, sms = 0;
+  CP_CUDA(cpk::push_ens_occupancy(b->precision, threads, b->push_smem, &per_sm));
+  if (per_sm < 1) return CP_ERR_ARG;
+  if (per_sm_req > 0) {
+    if (per_sm_req > per_sm) return CP_ERR_ARG;
+    per_sm = per_sm_req;
+  }
+  CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  const int grid = per_sm * sms;
+  if (grid > b->abs_grid) {  // absorbed-ion lists: one per CTA
+    cudaFree(b->abs);
+    b->abs = nullptr;
+    CP_TRY(alloc(&b->abs, cpk::abs_rec_ens_bytes() * static_cast<size_t>(grid) * b->abs_cap));
+    b->abs_grid = grid;
+  }
+  b->push_threads = threads;
+  b->push_grid = grid;
+  for (int m = 0; m < 2; ++m) {  // graphs carry the old shape
+    if (b->gexec[m]) cudaGraphExecDestroy(b->gexec[m]);
+    b->gexec[m] = nullptr;
+  }
+  return CP_OK;
+}
+
+int batch_init(cp_batch* b, int mode, double tol) {
+  for (cp_ctx* c : b->inst) {
+    c->ens_member = true;
+    CP_TRY(initialize(c, mode, tol));
+  }
+  std::vector<cpk::Bufs> hb(b->E);
+  b->n_max = 0;
+  for (int i = 0; i < b->E; ++i) {
+    hb[i] = make_bufs(b->inst[i]);
+    b->n_max = std::max(b->n_max, b->inst[i]->N);
+  }
+  CP_TRY(alloc(reinterpret_cast<void**>(&b->dBall), sizeof(cpk::Bufs) * b->E));
+  CP_CUDA(cudaMemcpyAsync(b->dBall, hb.data(), sizeof(cpk::Bufs) * b->E, cudaMemcpyHostToDevice,
+                          b->stream));
+  CP_TRY(alloc(reinterpret_cast<void**>(&b->dstatus), sizeof(int) * b->E));
+  b->push_smem = cpk::push_ens_smem_bytes(b->n_max, b->precision, b->E);
+  b->solve_smem = cpk::solve_smem_bytes(b->n_max, 1);
+  CP_CUDA(cpk::solve_ens_configure(b->precision, b->solve_smem));
+  int sms = 0;
+  CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  b->compact_grid = 2 * sms;
+  CP_TRY(batch_set_shape(b, 512, 0));
+  CP_CUDA(cudaStreamSynchronize(b->stream));
+  b->initialized = true;
+  return CP_OK;
+}
+
+cudaError_t batch_step_launches(cp_batch* b, cudaStream_t st, int mode, double tol) {
+  cudaError_t e = cpk::push_ens_launch(b->precision, b->push_threads, b->push_grid, b->push_smem,
+                                       b->dBall, b->E, b->n_max, b->abs, b->abs_cap, st);
+  if (e == cudaSuccess)
+    e = cpk::solve_ens_launch(b->precision, b->dBall, b->E, b->solve_smem, st, 1, mode, tol);
+  return e;
+}
+
+int batch_build_graph(cp_batch* b, int mode, double tol) {
+  if (b->gexec[mode] && b->gtol[mode] == tol) return CP_OK;
+  if (b->gexec[mode]) {
+    cudaGraphExecDestroy(b->gexec[mode]);
+    b->gexec[mode] = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CP_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < b->compact_every && e == cudaSuccess; ++k)
+    e = batch_step_launches(b, b->cap_stream, mode, tol);
+  if (e == cudaSuccess) e = cpk::compact_ens_launch(b->precision, b->dBall, b->E, b->compact_grid, b->cap_stream);
+  const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return CP_ERR_CUDA;
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&b->gexec[mode], g, 0);
+  cudaGraphDestroy(g);
+  CP_CUDA(e3);
+  b->gtol[mode] = tol;
+  return CP_OK;
+}
+
+// First non-zero instance status (0 if none); statuses gathered by one kernel.
+int batch_status(cp_batch* b, std::vector<int>* all) {
+  std::vector<int> st(b->E, 0);
+  CP_CUDA(cpk::status_ens_launch(b->dBall, b->E, b->dstatus, b->stream));
+  CP_CUDA(cudaMemcpyAsync(st.data(), b->dstatus, sizeof(int) * b->E, cudaMemcpyDeviceToHost, b->stream));
+  CP_CUDA(cudaStreamSynchronize(b->stream));
+  int first = 0;
+  for (int v : st)
+    if (v != 0 && first == 0) first = v;
+  if (all) *all = st;
+  return first;
+}
+
+int batch_steps(cp_batch* b, int mode, int32_t n_steps, double tol) {
+  if (!b || n_steps < 0 || !(tol > 0.0)) return CP_ERR_ARG;
+  CP_CUDA(cudaSetDevice(b->device));
+  b->launches = 0;
+  if (!b->initialized) CP_TRY(batch_init(b, mode, tol));
+  int64_t level = 0;
+  CP_CUDA(cudaMemcpyAsync(&level, &b->inst[0]->dS->level, sizeof(level), cudaMemcpyDeviceToHost,
+                          b->stream));
+  CP_CUDA(cudaStreamSynchronize(b->stream));
+  if (level + n_steps > b->max_steps) return CP_ERR_ARG;
+  int left = n_steps;
+  while (left > 0) {
+    if (b->since_compact == 0 && left >= b->compact_every) {
+      CP_TRY(batch_build_graph(b, mode, tol));
+      CP_CUDA(cudaGraphLaunch(b->gexec[mode], b->stream));
+      b->launches += 2 * b->compact_every + 2;
+      left -= b->compact_every;
+      continue;
+    }
+    CP_CUDA(batch_step_launches(b, b->stream, mode, tol));
+    b->launches += 2;
+    --left;
+    if (++b->since_compact == b->compact_every) {
+      CP_CUDA(cpk::compact_ens_launch(b->precision, b->dBall, b->E, b->compact_grid, b->stream));
+      b->launches += 2;
+      b->since_compact = 0;
+    }
+  }
+  return batch_status(b, nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cp_batch_create(int32_t n, const cp_gap* gaps, const cp_circuit* circuits,
+                    const cp_see_beam* sees, const cp_run* runs, void* stream, cp_batch** out) {
+  if (!out || !gaps || !circuits || !sees || !runs || n < 1 || n > cpk::ens_max_instances())
+    return CP_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (runs[i].precision != runs[0].precision || runs[i].max_steps != runs[0].max_steps ||
+        runs[i].compact_every != runs[0].compact_every || gaps[i].n_cells > 4096)
+      return CP_ERR_ARG;
+  }
+  cp_batch* b = new (std::nothrow) cp_batch();
+  if (!b) return CP_ERR_OOM;
+  if (cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return CP_ERR_CUDA;
+  }
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->E = n;
+  b->precision = runs[0].precision;
+  b->inst.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    cp_ctx* c = nullptr;
+    const int rc = cp_create(&gaps[i], &circuits[i], &sees[i], &runs[i], stream, &c);
+    if (rc != CP_OK) {
+      batch_free(b);
+      delete b;
+      return rc;
+    }
+    b->inst.push_back(c);
+  }
+  b->compact_every = b->inst[0]->compact_every;
+  b->max_steps = b->inst[0]->max_steps;
+  *out = b;
+  return CP_OK;
+}
+
+int cp_batch_set_particles(cp_batch* b, int32_t i, int32_t species, const double* x, const double* v,
+                           const uint32_t* id, int64_t n, int32_t units) {
+  if (!b || i < 0 || i >= b->E || b->initialized) return CP_ERR_ARG;
+  return cp_set_particles(b->inst[i], species, x, v, id, n, units);
+}
+
+int cp_batch_step_strict(cp_batch* b, int32_t n_steps, double residual_tol) {
+  return batch_steps(b, 0, n_steps, residual_tol);
+}
+
+int cp_batch_step_weak(cp_batch* b, int32_t n_steps) { return batch_steps(b, 1, n_steps, 1e300); }
+
+int cp_batch_read_history(cp_batch* b, int32_t i, int64_t first, int64_t n, cp_diag* out) {
+  if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;
+  return cp_read_history(b->inst[i], first, n, out);
+}
+
+int cp_batch_read_grid(cp_batch* b, int32_t i, double* phi, double* rho, double* E, int64_t* G,
+                       int32_t n_nodes) {
+  if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;
+  return cp_read_grid(b->inst[i], phi, rho, E, G, n_nodes);
+}
+
+int cp_batch_get_particles(cp_batch* b, int32_t i, int32_t species, double* xi, double* u,
+                           uint32_t* id, int64_t cap, int64_t* n) {
+  if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;
+  return cp_get_particles(b->inst[i], species, xi, u, id, cap, n);
+}
+
+int cp_batch_status(cp_batch* b, int32_t* status) {
+  if (!b || !status) return CP_ERR_ARG;
+  if (!b->initialized) {
+    for (int i = 0; i < b->E; ++i) status[i] = 0;
+    return CP_OK;
+  }
+  std::vector<int> all;
+  CP_CUDA(cudaSetDevice(b->device));
+  const int first = batch_status(b, &all);
+  if (first < 0 && all.empty()) return first;
+  for (int i = 0; i < b->E; ++i) status[i] = all[i];
+  return CP_OK;
+}
+
+int cp_batch_set_launch(cp_batch* b, int32_t threads, int32_t ctas_per_sm) {
+  if (!b || !b->initialized) return CP_ERR_ARG;
+  CP_CUDA(cudaSetDevice(b->device));
+  return batch_set_shape(b, threads, ctas_per_sm);
+}
+
+int cp_batch_get_launch(cp_batch* b, int32_t* threads, int32_t* grid) {
+  if (!b || !threads || !grid || !b->initialized) return CP_ERR_ARG;
+  *threads = b->push_threads;
+  *grid = b->push_grid;
+  return CP_OK;
+}
+
+int cp_batch_autotune(cp_batch* b, int32_t steps_per_shape, int32_t mode, double residual_tol,
+                      int32_t* threads, int32_t* ctas_per_sm, double* push_ms) {
+  if (!b || steps_per_shape < 1 || (mode != 0 && mode != 1) || !(residual_tol > 0.0))
+    return CP_ERR_ARG;
+  CP_CUDA(cudaSetDevice(b->device));
+  if (!b->initialized) CP_TRY(batch_init(b, mode, residual_tol));
+  const double tol = (mode == 0) ? residual_tol : 1e300;
+  const int shapes[][2] = {{512, 2}, {512, 1}, {256, 2}, {256, 1}, {1024, 1}};
+  double best = 1e300;
+  int best_t = 512, best_p = 0;
+  cudaEvent_t e0, e1;
+  CP_CUDA(cudaEventCreate(&e0));
+  CP_CUDA(cudaEventCreate(&e1));
+  int rc = CP_OK;
+  for (const auto& sh : shapes) {
+    if (batch_set_shape(b, sh[0], sh[1]) != CP_OK) continue;  // shape not resident on this device
+    int64_t level = 0;
+    rc = cuda_rc(cudaMemcpyAsync(&level, &b->inst[0]->dS->level, sizeof(level),
+                                 cudaMemcpyDeviceToHost, b->stream));
+    if (rc == CP_OK) rc = cuda_rc(cudaStreamSynchronize(b->stream));
+    if (rc != CP_OK) break;
+    if (level + steps_per_shape > b->max_steps) {
+      rc = CP_ERR_ARG;
+      break;
+    }
+    // ordinary steps of the run (results do not depend on the launch shape);
+    // the push of each is timed
+    double ms_sum = 0.0;
+    for (int k = 0; k < steps_per_shape && rc == CP_OK; ++k) {
+      rc = cuda_rc(cudaEventRecord(e0, b->stream));
+      if (rc == CP_OK)
+        rc = cuda_rc(cpk::push_ens_launch(b->precision, b->push_threads, b->push_grid, b->push_smem,
+                                          b->dBall, b->E, b->n_max, b->abs, b->abs_cap, b->stream));
+      if (rc == CP_OK) rc = cuda_rc(cudaEventRecord(e1, b->stream));
+      if (rc == CP_OK)
+        rc = cuda_rc(cpk::solve_ens_launch(b->precision, b->dBall, b->E, b->solve_smem, b->stream,
+                                           1, mode, tol));
+      if (rc == CP_OK) rc = cuda_rc(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      if (rc == CP_OK) rc = cuda_rc(cudaEventElapsedTime(&ms, e0, e1));
+      ms_sum += ms;
+      if (++b->since_compact == b->compact_every && rc == CP_OK) {
+        rc = cuda_rc(cpk::compact_ens_launch(b->precision, b->dBall, b->E, b->compact_grid, b->stream));
+        b->since_compact = 0;
+      }
+    }
+    if (rc != CP_OK) break;
+    const double avg = ms_sum / steps_per_shape;
+    if (avg < best) {
+      best = avg;
+      best_t = b->push_threads;
+      best_p = b->push_grid;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CP_OK) return rc;
+  int sms = 1;
+  CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  CP_TRY(batch_set_shape(b, best_t, best_p / sms));
+  if (threads) *threads = best_t;
+  if (ctas_per_sm) *ctas_per_sm = best_p / sms;
+  if (push_ms) *push_ms = best;
+  const int st = batch_status(b, nullptr);
+  return st;
+}
+
+int cp_batch_get_level(cp_batch* b, int32_t i, int64_t* level) {
+  if (!b || !level || i < 0 || i >= b->E) return CP_ERR_ARG;
+  return cp_get_level(b->inst[i], level);
+}
+
+int cp_batch_last_launch_count(cp_batch* b, int64_t* launches) {
+  if (!b || !launches) return CP_ERR_ARG;
+  *launches = b->launches;
+  return CP_OK;
+}
+
+void cp_batch_destroy(cp_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  delete b;
 }
 
 }  // extern "C"

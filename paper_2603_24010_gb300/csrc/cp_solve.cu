@@ -343,8 +343,10 @@ __device__ __noinline__ void predictor_update(const Bufs& B, const double* sc, b
   }
 }
 
+// The solve of one instance by the CTAs of one cluster (a cluster of one CTA
+// in the ensemble launch).
 template <typename real>
-__global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push, int mode, double tol) {
+__device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode, double tol) {
   using real2 = typename Pair<real>::type;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
@@ -699,7 +701,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
   // barrier D: no rank leaves (freeing its shared memory) before every
   // rank's remote reads are done
   cl.barrier_wait(std::move(done_tok));
-  if (rank == 1) {
+  if (rank == 1) {  // the predictor runs beside rank 0's commit
     if (B.net != nullptr && do_push) predictor_update(B, sc, strict_rlc, phi0_fin);
     return;
   }
@@ -793,6 +795,24 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push,
     S->n_alloc[s] = na4;
     S->n_proc[s] = na4;
   }
+  if (nr == 1 && B.net != nullptr && do_push) {  // a one-CTA solve runs the predictor itself
+    __syncthreads();
+    predictor_update(B, sc, strict_rlc, phi0_fin);
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kSolveThreads, 1) k_solve(Bufs B, int do_push, int mode, double tol) {
+  solve_body<real>(B, do_push, mode, tol);
+}
+
+// Ensemble: CTA i solves instance i (launched without clusters, so each CTA
+// is a cluster of one).
+template <typename real>
+__global__ void __launch_bounds__(kSolveThreads, 1)
+k_solve_ens(const Bufs* __restrict__ Ball, int do_push, int mode, double tol) {
+  const Bufs B = Ball[blockIdx.x];
+  solve_body<real>(B, do_push, mode, tol);
 }
 
 // ---------------------------------------------------------------------------
@@ -842,6 +862,30 @@ cudaError_t solve_cluster_size(int precision, int N, int* ctas) {
     *ctas = kSolveCtasMax;
   cudaGetLastError();
   return cudaSuccess;
+}
+
+cudaError_t solve_ens_configure(int precision, size_t smem) {
+  if (precision == CP_FP32)
+    return cudaFuncSetAttribute(k_solve_ens<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem));
+  return cudaFuncSetAttribute(k_solve_ens<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem));
+}
+
+cudaError_t solve_ens_launch(int precision, const Bufs* Ball, int n_inst, size_t smem,
+                             cudaStream_t st, int do_push, int mode, double tol) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_inst, 1, 1);
+  cfg.blockDim = dim3(kSolveThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision == CP_FP32) return cudaLaunchKernelEx(&cfg, k_solve_ens<float>, Ball, do_push, mode, tol);
+  return cudaLaunchKernelEx(&cfg, k_solve_ens<double>, Ball, do_push, mode, tol);
 }
 
 cudaError_t solve_launch(int precision, const Bufs& B, int ctas, size_t smem, cudaStream_t st,

@@ -27,7 +27,11 @@ EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "c
            "cp_read_timing", "cp_read_launch_times", "cp_push_ions_noalloc", "cp_set_predictor",
            "cp_step_weak_learned", "cp_predictor_samples", "cp_mlp_init", "cp_mlp_scales",
            "cp_mlp_normalize", "cp_mlp_forward", "cp_mlp_work_floats", "cp_mlp_loss_grad",
-           "cp_mlp_adam", "cp_destroy", "cp_status_str")
+           "cp_mlp_adam", "cp_batch_create", "cp_batch_set_particles", "cp_batch_step_strict",
+           "cp_batch_step_weak", "cp_batch_read_history", "cp_batch_read_grid",
+           "cp_batch_get_particles", "cp_batch_status", "cp_batch_get_level",
+           "cp_batch_last_launch_count", "cp_batch_set_launch", "cp_batch_get_launch",
+           "cp_batch_autotune", "cp_batch_destroy", "cp_destroy", "cp_status_str")
 STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 40, 64, 2, 11074
 PRED_WINDOW, PRED_FEATURES = 8, 5
@@ -117,6 +121,24 @@ def lib():
         L.cp_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int64, fp, fp, fp, vp]
         L.cp_mlp_adam.argtypes = [fp, fp, fp, fp, C.c_int64, C.c_float, C.c_float, C.c_float,
                                   C.c_float, vp]
+        L.cp_batch_create.argtypes = [C.c_int32, C.POINTER(cp_gap), C.POINTER(cp_circuit),
+                                      C.POINTER(cp_see_beam), C.POINTER(cp_run), vp, C.POINTER(vp)]
+        L.cp_batch_set_particles.argtypes = [vp, C.c_int32, C.c_int32, dp, dp, u32p, C.c_int64,
+                                             C.c_int32]
+        L.cp_batch_step_strict.argtypes = [vp, C.c_int32, C.c_double]
+        L.cp_batch_step_weak.argtypes = [vp, C.c_int32]
+        L.cp_batch_read_history.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.POINTER(cp_diag)]
+        L.cp_batch_read_grid.argtypes = [vp, C.c_int32, dp, dp, dp, i64p, C.c_int32]
+        L.cp_batch_get_particles.argtypes = [vp, C.c_int32, C.c_int32, dp, dp, u32p, C.c_int64, i64p]
+        L.cp_batch_status.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.cp_batch_get_level.argtypes = [vp, C.c_int32, i64p]
+        L.cp_batch_last_launch_count.argtypes = [vp, i64p]
+        L.cp_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
+        L.cp_batch_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.cp_batch_autotune.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32), dp]
+        L.cp_batch_destroy.argtypes = [vp]
+        L.cp_batch_destroy.restype = None
         L.cp_destroy.argtypes = [vp]
         L.cp_destroy.restype = None
         L.cp_status_str.argtypes = [C.c_int]
@@ -413,3 +435,112 @@ def diag_to_dict(arr):
             dt = np.int64 if typ is C.c_int64 else np.float64
             out[name] = np.array([getattr(arr[k], name) for k in range(n)], dtype=dt)
     return out
+
+
+class Batch:
+    """An ensemble of independent gap instances driven through the cp_batch_* calls."""
+
+    def __init__(self, cfgs, max_steps, compact_every=0, stream=None):
+        n = len(cfgs)
+        self.cfgs = [dict(c) for c in cfgs]
+        self.n = n
+        gaps, circs, sees, runs = (cp_gap * n)(), (cp_circuit * n)(), (cp_see_beam * n)(), (cp_run * n)()
+        for i, cfg in enumerate(cfgs):
+            g, c, s, r = structs_from_config(cfg, max_steps=max_steps, compact_every=compact_every)
+            gaps[i], circs[i], sees[i], runs[i] = g, c, s, r
+        h = C.c_void_p()
+        _check("cp_batch_create", lib().cp_batch_create(
+            n, gaps, circs, sees, runs, C.c_void_p(current_stream() if stream is None else stream),
+            C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, i, species, xi, u, ids=None, units=UNITS_CELL):
+        xi = np.ascontiguousarray(xi, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        _check("cp_batch_set_particles", lib().cp_batch_set_particles(
+            self.h, int(i), int(species), _dp(xi), _dp(u), _u32p(ids), xi.size, int(units)))
+
+    def step(self, mode, n_steps, tol=1e-12):
+        """Returns the first non-zero instance status (0 if none)."""
+        if mode == STRICT:
+            return lib().cp_batch_step_strict(self.h, int(n_steps), float(tol))
+        if mode == WEAK:
+            return lib().cp_batch_step_weak(self.h, int(n_steps))
+        raise ValueError("the ensemble runs strict or weak coupling")
+
+    def level_of(self, i):
+        lv = C.c_int64()
+        _check("cp_batch_get_level", lib().cp_batch_get_level(self.h, int(i), C.byref(lv)))
+        return lv.value
+
+    @property
+    def level(self):
+        return self.level_of(0)
+
+    def history(self, i, first=0, n=None):
+        if n is None:
+            n = self.level_of(i) + 1 - first
+        arr = (cp_diag * int(n))()
+        _check("cp_batch_read_history", lib().cp_batch_read_history(self.h, int(i), int(first),
+                                                                    int(n), arr))
+        return diag_to_dict(arr)
+
+    def grid(self, i):
+        N = int(self.cfgs[i]["n_cells"])
+        phi, rho, E = np.zeros(N + 1), np.zeros(N + 1), np.zeros(N)
+        G = np.zeros(N + 1, dtype=np.int64)
+        _check("cp_batch_read_grid", lib().cp_batch_read_grid(self.h, int(i), _dp(phi), _dp(rho),
+                                                              _dp(E), _i64p(G), N + 1))
+        return dict(phi=phi, rho=rho, E=E, G=G)
+
+    def particles(self, i, species):
+        n = C.c_int64()
+        rc = lib().cp_batch_get_particles(self.h, int(i), int(species), None, None, None, 0,
+                                          C.byref(n))
+        if rc not in (OK, ERR_CAPACITY):
+            _check("cp_batch_get_particles", rc)
+        cap = max(n.value, 1)
+        xi, u = np.zeros(cap), np.zeros(cap)
+        ids = np.zeros(cap, dtype=np.uint32)
+        _check("cp_batch_get_particles", lib().cp_batch_get_particles(
+            self.h, int(i), int(species), _dp(xi), _dp(u), _u32p(ids), cap, C.byref(n)))
+        m = n.value
+        return xi[:m], u[:m], (ids[:m] if species == IONS else None)
+
+    def status(self):
+        st = (C.c_int32 * self.n)()
+        _check("cp_batch_status", lib().cp_batch_status(self.h, st))
+        return np.array(st[:], dtype=np.int32)
+
+    def set_launch(self, threads, ctas_per_sm=0):
+        return lib().cp_batch_set_launch(self.h, int(threads), int(ctas_per_sm))
+
+    def launch(self):
+        t, g = C.c_int32(), C.c_int32()
+        _check("cp_batch_get_launch", lib().cp_batch_get_launch(self.h, C.byref(t), C.byref(g)))
+        return t.value, g.value
+
+    def autotune(self, steps_per_shape, mode=STRICT, tol=1e-12):
+        t, p = C.c_int32(), C.c_int32()
+        ms = C.c_double()
+        rc = lib().cp_batch_autotune(self.h, int(steps_per_shape), int(mode), float(tol),
+                                     C.byref(t), C.byref(p), C.byref(ms))
+        return rc, t.value, p.value, ms.value
+
+    def last_launch_count(self):
+        n = C.c_int64()
+        _check("cp_batch_last_launch_count", lib().cp_batch_last_launch_count(self.h, C.byref(n)))
+        return n.value

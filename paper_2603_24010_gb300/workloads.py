@@ -19,6 +19,11 @@ injection profile are not available, so these parameter sets stand in):
 * ``gap_1d_fp32_thinned``: the same physics with `factor` times fewer
   macroparticles of `factor` times the weight (loaded pairs and beam alike):
   the predictor's training and evaluation runs.
+* ``ensemble``: independent 5 mm gaps with cells log-uniform in 256-4096,
+  initial macroparticles log-uniform in 1e4-2e6, V0 uniform in 50-200 kV,
+  C uniform in 20-500 pF, SEE scale uniform in 0-2 (every 8th instance
+  SEE-free), mono-energetic beam uniform in 5-50 keV at
+  max(50, N_init/2000) ions per step, dt = 1 ps, FP32 particles.
 """
 import math
 
@@ -72,6 +77,31 @@ def gap_1d_fp32_thinned(seed=0, factor=25, steps=20000):
     cfg["beam_mode"] = int(rng.integers(0, 2))
     cfg["name"] = "gap_1d_fp32_thinned"
     return cfg
+
+
+def ensemble(n_inst=512, seed=0, steps=10000, thin=1, n_cells_max=4096):
+    """Instances of the ensemble workload; `thin` divides every particle count
+    (weights scaled up to keep the densities and beam currents)."""
+    rng = np.random.default_rng([seed, 0xE75])
+    out = []
+    for i in range(n_inst):
+        n_cells = int(round(math.exp(rng.uniform(math.log(256), math.log(n_cells_max)))))
+        n_init = math.exp(rng.uniform(math.log(1e4), math.log(2e6)))
+        n_pairs = max(16, int(n_init / 2 / thin))
+        beam = max(1, int(max(50.0, n_init / 2000.0) / thin))
+        cfg = _base(n_cells, n_pairs, 1e-12, steps, beam, FP32, seed=seed * 100003 + i)
+        C = rng.uniform(20e-12, 500e-12)
+        cfg["C"] = C
+        cfg["area"] = C * cfg["d"] / EPS0
+        cfg["weight"] = cfg["n0"] * cfg["d"] * cfg["area"] / n_pairs
+        cfg["V0"] = rng.uniform(50e3, 200e3)
+        scale = rng.uniform(0.0, 2.0)
+        cfg["see_scale"] = 0.0 if i % 8 == 7 else scale
+        cfg["beam_E_eV"] = rng.uniform(5e3, 50e3)
+        cfg["beam_mode"] = 0
+        cfg["name"] = "ensemble[%d]" % i
+        out.append(cfg)
+    return out
 
 
 def scaled(cfg, **over):

@@ -1,0 +1,179 @@
+"""The ensemble path (cp_batch_*) against single-instance contexts.
+
+Every instance of an ensemble must give bit for bit what it gives as a
+context of its own: the per-particle arithmetic is the same, the charge is
+integer, the draws are counter-based and the solve is an exact integer scan.
+Checked on instances of uneven size and physics (the ensemble workload,
+thinned), over enough steps for graph replays and removals, in strict and
+weak coupling, for every launch shape of the autotuner, and with one
+instance stopping on a capacity error while the others go on.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_24010_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_24010_gb300 import native
+    native.lib()
+    return torch, native
+
+
+def instances(n=6, seed=0, thin=400, n_cells_max=1024):
+    cfgs = W.ensemble(n, seed=seed, steps=300, thin=thin, n_cells_max=n_cells_max)
+    for c in cfgs:  # short runs: a thinner, faster-crossing gap so impacts happen
+        c["d"] = 5e-4
+        c["area"] = c["C"] * c["d"] / c["eps0"]
+        c["weight"] = c["n0"] * c["d"] * c["area"] / c["n_pairs"]
+        c["see_scale"] *= 4.0
+    return cfgs
+
+
+def load(cfg):
+    xi, ue, ui = W.load_pairs(cfg)
+    return xi, ue, ui, np.arange(xi.size, dtype=np.uint32)
+
+
+def single_run(native, cfg, mode, steps):
+    g = native.Gap(cfg, max_steps=steps)
+    xi, ue, ui, ids = load(cfg)
+    g.set_particles(native.ELECTRONS, xi, ue)
+    g.set_particles(native.IONS, xi, ui, ids)
+    rc = native.cp_step_strict(g.ctx, steps, 1e-12) if mode == 0 else native.cp_step_weak(g.ctx, steps)
+    out = dict(rc=rc, h=g.history(), grid=g.grid(),
+               parts=[g.particles(s) for s in range(3)])
+    g.close()
+    return out
+
+
+def batch_of(native, cfgs, steps, capacity=None):
+    b = native.Batch(cfgs, max_steps=steps)
+    for i, cfg in enumerate(cfgs):
+        xi, ue, ui, ids = load(cfg)
+        b.set_particles(i, native.ELECTRONS, xi, ue)
+        b.set_particles(i, native.IONS, xi, ui, ids)
+    return b
+
+
+def same_particles(a, b):
+    for s in range(3):
+        xa, ua = a[s][0], a[s][1]
+        xb, ub = b[s][0], b[s][1]
+        assert xa.size == xb.size, s
+        oa, ob = np.lexsort((ua, xa)), np.lexsort((ub, xb))
+        np.testing.assert_array_equal(xa[oa], xb[ob])
+        np.testing.assert_array_equal(ua[oa], ub[ob])
+
+
+def check_same(native, b, i, ref):
+    h = b.history(i)
+    for k in ("V_gap", "I_circ", "Q_surf", "Q_circ", "Q_conv", "residual"):
+        np.testing.assert_array_equal(h[k], ref["h"][k], err_msg=k)
+    for k in ("absorbed", "emitted", "injected", "n_live", "conv_count"):
+        np.testing.assert_array_equal(h[k], ref["h"][k], err_msg=k)
+    gr = b.grid(i)
+    np.testing.assert_array_equal(gr["G"], ref["grid"]["G"])
+    np.testing.assert_array_equal(gr["phi"], ref["grid"]["phi"])
+    same_particles([b.particles(i, s) for s in range(3)], ref["parts"])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ensemble_equals_single_instances(env, mode):
+    torch, native = env
+    cfgs = instances()
+    steps = 200  # three removals; graph replays of 64 steps
+    refs = [single_run(native, c, mode, steps) for c in cfgs]
+    b = batch_of(native, cfgs, steps)
+    assert b.step(mode, steps) == native.OK
+    assert b.last_launch_count() > 0
+    assert sum(r["h"]["emitted"][:, 0].sum() for r in refs) > 100  # SEE happened
+    for i in range(len(cfgs)):
+        check_same(native, b, i, refs[i])
+    b.close()
+
+
+def test_every_launch_shape_gives_the_same_bits(env):
+    torch, native = env
+    cfgs = instances(n=5, seed=3)
+    steps = 90
+    ref = None
+    shapes = [(512, 2), (512, 1), (256, 2), (256, 1), (1024, 1)]
+    ran = 0
+    for threads, per_sm in shapes:
+        b = batch_of(native, cfgs, steps)
+        assert b.step(0, 1) == native.OK  # first step: set-up with the default shape
+        if b.set_launch(threads, per_sm) != native.OK:
+            b.close()
+            continue
+        assert b.launch()[0] == threads
+        assert b.step(0, steps - 1) == native.OK
+        hs = [b.history(i) for i in range(len(cfgs))]
+        b.close()
+        ran += 1
+        if ref is None:
+            ref = hs
+            continue
+        for i in range(len(cfgs)):
+            np.testing.assert_array_equal(hs[i]["V_gap"], ref[i]["V_gap"])
+            np.testing.assert_array_equal(hs[i]["n_live"], ref[i]["n_live"])
+    assert ran >= 3
+
+
+def test_autotune_keeps_the_run(env):
+    torch, native = env
+    cfgs = instances(n=4, seed=5)
+    steps = 120
+    refs = [single_run(native, c, 0, steps) for c in cfgs]
+    b = batch_of(native, cfgs, steps)
+    rc, threads, per_sm, ms = b.autotune(4)
+    assert rc == native.OK and threads in (256, 512, 1024) and per_sm >= 1 and ms > 0
+    assert b.launch()[0] == threads
+    lv = b.level
+    assert lv >= 4 * 3  # the tuner's trial steps are steps of the run
+    assert b.step(0, steps - lv) == native.OK
+    for i in range(len(cfgs)):
+        check_same(native, b, i, refs[i])
+    b.close()
+
+
+def test_a_failing_instance_stops_alone(env):
+    torch, native = env
+    cfgs = instances(n=4, seed=7)
+    steps = 100
+    # instance 2: room for its loaded ions and a few beam steps only
+    cfgs[2] = dict(cfgs[2])
+    cap_ions = cfgs[2]["n_pairs"] + 4 * cfgs[2]["beam_per_step"]
+    # the batch takes the capacities of its runs: instance 2 gets a small ion store
+    n = len(cfgs)
+    G, Cc, S, R = ((native.cp_gap * n)(), (native.cp_circuit * n)(), (native.cp_see_beam * n)(),
+                   (native.cp_run * n)())
+    for i, cfg in enumerate(cfgs):
+        cap = (0, (cap_ions + 64 + 3) // 4 * 4, 0) if i == 2 else (0, 0, 0)
+        g_, c_, s_, r_ = native.structs_from_config(cfg, capacity=cap, max_steps=steps)
+        G[i], Cc[i], S[i], R[i] = g_, c_, s_, r_
+    import ctypes as C
+    h = C.c_void_p()
+    assert native.lib().cp_batch_create(n, G, Cc, S, R, C.c_void_p(native.current_stream()),
+                                        C.byref(h)) == native.OK
+    bb = native.Batch.__new__(native.Batch)
+    bb.h, bb.n, bb.cfgs = h, n, cfgs
+    for i, cfg in enumerate(cfgs):
+        xi, ue, ui, ids = load(cfg)
+        bb.set_particles(i, native.ELECTRONS, xi, ue)
+        bb.set_particles(i, native.IONS, xi, ui, ids)
+    rc = bb.step(0, steps)
+    assert rc == native.ERR_CAPACITY
+    st = bb.status()
+    assert st[2] == native.ERR_CAPACITY and np.all(st[[0, 1, 3]] == 0)
+    for i in (0, 1, 3):
+        ref = single_run(native, cfgs[i], 0, steps)
+        np.testing.assert_array_equal(bb.history(i)["V_gap"], ref["h"]["V_gap"])
+    assert bb.history(2)["V_gap"].size < steps + 1  # stopped early
+    bb.close()
