@@ -19,6 +19,7 @@ of this build, written from the paper) on the host cores on a bounded sample
 of the same workload.
 """
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -242,7 +243,7 @@ def run_native(args, rank, world):
     g2.close()
     es = 4 if cfg["precision"] == W.FP32 else 8
     h2d = (xe.size + xI.size) * 2 * es + xI.size * 4
-    d2h = (K + 1) * 208
+    d2h = (K + 1) * ctypes.sizeof(native.cp_diag)
 
     if world > 1:
         t = torch.tensor([ms, e2e_s * 1e3], device="cuda", dtype=torch.float64)
@@ -272,6 +273,108 @@ def run_native(args, rank, world):
                 d2h=d2h, launches=launches, kernel_ms=kms.tolist(), kernel_n=kn.tolist(),
                 avg_launch_ms=avg_launch_ms, achieved=achieved, peak=peak, peak_kind=peak_kind,
                 clocks=clk, bpp=bpp, n_sel=n_sel, traffic=traffic, frac_psteps_above_l2=float(live[state > 129e6].sum()) / max(psteps, 1))
+
+
+# ---------------------------------------------------------------- ensemble
+def run_ensemble(args, K, Wm):
+    """The ensemble workload: 512 independent gaps of uneven size advanced by
+    one persistent push and one solve launch per step (CUDA graph).  Strict
+    coupling is timed (the line's value); weak coupling is run on the same
+    instances and reported beside it."""
+    import torch
+    from paper_2603_24010_gb300 import native
+    n_inst = args.ensemble_instances
+    total = Wm + K + 1 + 5 * args.tune_steps
+    cfgs = W.ensemble(n_inst, seed=args.seed, steps=total)
+    stream = torch.cuda.current_stream()
+    loads = []
+    for cfg in cfgs:
+        xi, ue, ui = W.load_pairs(cfg)
+        xe, ue = W.as_precision(xi, ue, cfg["n_cells"], W.FP32)
+        xo, ui = W.as_precision(xi, ui, cfg["n_cells"], W.FP32)
+        loads.append((xe, ue, xo, ui))
+    out = {}
+    for mode, name in ((native.STRICT, "strict"), (native.WEAK, "weak")):
+        b = native.Batch(cfgs, max_steps=total, stream=stream.cuda_stream)
+        for i, (xe, ue, xo, ui) in enumerate(loads):
+            b.set_particles(i, native.ELECTRONS, xe, ue)
+            b.set_particles(i, native.IONS, xo, ui, np.arange(xo.size, dtype=np.uint32))
+        rc = b.step(mode, Wm)
+        tune = b.autotune(args.tune_steps, mode)
+        lv0 = b.level
+        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc2 = b.step(mode, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop()
+        launches = b.last_launch_count()
+        psteps = 0
+        for i in range(n_inst):
+            h = b.history(i, lv0, K)
+            psteps += int(h["n_live"].sum())
+        entry = dict(ms=ms, psteps=psteps, launches=launches, rc=[rc, tune[0], rc2],
+                     shape={"threads": tune[1], "ctas_per_sm": tune[2], "push_ms": tune[3]},
+                     clocks=clk)
+        if mode == native.STRICT:  # a short per-kernel timed pass for the roofline
+            b.enable_timing(True)
+            lv1 = b.level
+            Kt = min(args.ensemble_timed_steps, total - lv1)
+            b.step(mode, Kt)
+            kms, kn = b.timing()
+            b.enable_timing(False)
+            live_t = sum(int(b.history(i, lv1, Kt)["n_live"].sum()) for i in range(n_inst))
+            entry.update(kernel_ms=kms.tolist(), kernel_n=kn.tolist(), timed_psteps=live_t)
+        b.close()
+        out[name] = entry
+    tot_init = sum(2 * c["n_pairs"] for c in cfgs)
+    cells = [c["n_cells"] for c in cfgs]
+    out["desc"] = ("ensemble: %d gaps, cells %d-%d (log-uniform 256-4096), %.3g initial "
+                   "macroparticles (log-uniform 1e4-2e6 each), V0 50-200 kV, C 20-500 pF, SEE "
+                   "scale 0-2 (every 8th 0), mono beam 5-50 keV at max(50, N/2000) ions/step, "
+                   "dt 1 ps, FP32; %d warm-up + %d tuner + %d timed steps"
+                   % (n_inst, min(cells), max(cells), tot_init, Wm, 5 * args.tune_steps, K))
+    return out
+
+
+def ensemble_main(args, config):
+    import torch  # noqa: F401
+    from paper_2603_24010_gb300 import native  # noqa: F401
+    K = args.steps if args.steps is not None else 10000
+    Wm = args.warmup
+    r = run_ensemble(args, K, Wm)
+    st = r["strict"]
+    value = st["psteps"] / (st["ms"] * 1e-3)
+    peak, peak_kind = measured_peaks()
+    kms, kn = st["kernel_ms"], st["kernel_n"]
+    achieved = 16.0 * st["timed_psteps"] / (kms[0] * 1e-3) / 1e9
+    config = dict(config)
+    config["workload"] = r["desc"]
+    config["l2"] = "inputs larger than L2 (about 3 GB of particle state), no flush"
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": 1, "steps": K,
+        "warmup": Wm, "ms_per_step": st["ms"] / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "gpu_launches": st["launches"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_push_ens",
+                     "peak_source": peak_kind, "bytes_per_particle_step": 16,
+                     "push_avg_ms": kms[0] / max(kn[0], 1), "solve_avg_ms": kms[1] / max(kn[1], 1),
+                     "removal_avg_ms": kms[2] / max(kn[2], 1),
+                     "source": "per-launch CUDA events over %d steps after the timed region"
+                               % kn[0]},
+        "clocks": st["clocks"],
+        "autotuned_shape": st["shape"],
+        "weak": {"value": r["weak"]["psteps"] / (r["weak"]["ms"] * 1e-3),
+                 "ms_per_step": r["weak"]["ms"] / K, "shape": r["weak"]["shape"]},
+        "status": {"strict": st["rc"], "weak": r["weak"]["rc"]},
+        "particle_steps": st["psteps"],
+    }
+    print(json.dumps(line))
 
 
 # ---------------------------------------------------------------- coupling
@@ -360,7 +463,8 @@ def oracle_sample(cfg, K, Wm, budget_s, rate_guess=4e7):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 20000; 10000 for the ensemble)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--workload", default="gap_1d_fp32_large")
@@ -377,9 +481,17 @@ def main():
     ap.add_argument("--coupling-steps", type=int, default=20000)
     ap.add_argument("--coupling-factor", type=int, default=25)
     ap.add_argument("--coupling-iters", type=int, default=3000)
+    ap.add_argument("--ensemble-instances", type=int, default=512)
+    ap.add_argument("--ensemble-timed-steps", type=int, default=200)
+    ap.add_argument("--tune-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload == "ensemble":
+        ensemble_main(args, {"parallelism": "1 GPU"})
+        return
+    if args.steps is None:
+        args.steps = 20000
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     cfg = workload(args.workload, args.seed, pairs=args.pairs)

@@ -401,6 +401,12 @@ int cp_batch_status(cp_batch* b, int32_t* status /* n entries */);
 int cp_batch_get_level(cp_batch* b, int32_t i, int64_t* level);
 int cp_batch_last_launch_count(cp_batch* b, int64_t* launches);
 
+/* Per-kernel timing of the ensemble, as cp_enable_timing / cp_read_timing:
+   while on, steps launch each kernel directly between CUDA events; the
+   totals are of the push (k = 0), the solve (1) and the removal (2). */
+int cp_batch_enable_timing(cp_batch* b, int32_t on);
+int cp_batch_read_timing(cp_batch* b, double ms[3], int64_t n[3]);
+
 /* Launch shape of the ensemble push: threads per CTA (256, 512 or 1024) and
    CTAs per SM (0 = as many as fit).  Valid after the first step.
    Errors: CP_ERR_ARG if the shape cannot be resident. */

@@ -877,11 +877,17 @@ struct cp_batch {
   double gtol[2] = {0.0, 0.0};
   int64_t launches = 0;
   int* dstatus = nullptr;
+  bool timing = false;
+  double t_ms[3] = {0.0, 0.0, 0.0};  // push, solve, removal
+  int64_t t_n[3] = {0, 0, 0};
+  std::vector<cudaEvent_t> ev;
 };
 
 namespace {
 
 void batch_free(cp_batch* b) {
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  b->ev.clear();
   for (int m = 0; m < 2; ++m)
     if (b->gexec[m]) cudaGraphExecDestroy(b->gexec[m]);
   cudaFree(b->dBall);
@@ -991,6 +997,49 @@ int batch_status(cp_batch* b, std::vector<int>* all) {
   return first;
 }
 
+// Steps launched one kernel at a time between CUDA events (timing mode).
+int batch_steps_timed(cp_batch* b, int mode, int32_t n_steps, double tol) {
+  std::vector<std::pair<int, size_t>> rec;
+  auto timed = [&](int which) -> int {
+    const size_t k = rec.size() * 2;
+    while (b->ev.size() < k + 2) {
+      cudaEvent_t e;
+      CP_CUDA(cudaEventCreate(&e));
+      b->ev.push_back(e);
+    }
+    CP_CUDA(cudaEventRecord(b->ev[k], b->stream));
+    if (which == 0)
+      CP_CUDA(cpk::push_ens_launch(b->precision, b->push_threads, b->push_grid, b->push_smem,
+                                   b->dBall, b->E, b->n_max, b->abs, b->abs_cap, b->stream));
+    else if (which == 1)
+      CP_CUDA(cpk::solve_ens_launch(b->precision, b->dBall, b->E, b->solve_smem, b->stream, 1,
+                                    mode, tol));
+    else
+      CP_CUDA(cpk::compact_ens_launch(b->precision, b->dBall, b->E, b->compact_grid, b->stream));
+    CP_CUDA(cudaEventRecord(b->ev[k + 1], b->stream));
+    rec.push_back({which, k});
+    return CP_OK;
+  };
+  for (int k = 0; k < n_steps; ++k) {
+    CP_TRY(timed(0));
+    CP_TRY(timed(1));
+    b->launches += 2;
+    if (++b->since_compact == b->compact_every) {
+      CP_TRY(timed(2));
+      b->launches += 2;
+      b->since_compact = 0;
+    }
+  }
+  CP_CUDA(cudaStreamSynchronize(b->stream));
+  for (const auto& r : rec) {
+    float ms = 0.f;
+    CP_CUDA(cudaEventElapsedTime(&ms, b->ev[r.second], b->ev[r.second + 1]));
+    b->t_ms[r.first] += ms;
+    b->t_n[r.first] += 1;
+  }
+  return CP_OK;
+}
+
 int batch_steps(cp_batch* b, int mode, int32_t n_steps, double tol) {
   if (!b || n_steps < 0 || !(tol > 0.0)) return CP_ERR_ARG;
   CP_CUDA(cudaSetDevice(b->device));
@@ -1001,6 +1050,10 @@ int batch_steps(cp_batch* b, int mode, int32_t n_steps, double tol) {
                           b->stream));
   CP_CUDA(cudaStreamSynchronize(b->stream));
   if (level + n_steps > b->max_steps) return CP_ERR_ARG;
+  if (b->timing) {
+    CP_TRY(batch_steps_timed(b, mode, n_steps, tol));
+    return batch_status(b, nullptr);
+  }
   int left = n_steps;
   while (left > 0) {
     if (b->since_compact == 0 && left >= b->compact_every) {
@@ -1189,6 +1242,25 @@ int cp_batch_autotune(cp_batch* b, int32_t steps_per_shape, int32_t mode, double
 int cp_batch_get_level(cp_batch* b, int32_t i, int64_t* level) {
   if (!b || !level || i < 0 || i >= b->E) return CP_ERR_ARG;
   return cp_get_level(b->inst[i], level);
+}
+
+int cp_batch_enable_timing(cp_batch* b, int32_t on) {
+  if (!b) return CP_ERR_ARG;
+  b->timing = (on != 0);
+  for (int k = 0; k < 3; ++k) {
+    b->t_ms[k] = 0.0;
+    b->t_n[k] = 0;
+  }
+  return CP_OK;
+}
+
+int cp_batch_read_timing(cp_batch* b, double ms[3], int64_t n[3]) {
+  if (!b || !ms || !n) return CP_ERR_ARG;
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = b->t_ms[k];
+    n[k] = b->t_n[k];
+  }
+  return CP_OK;
 }
 
 int cp_batch_last_launch_count(cp_batch* b, int64_t* launches) {

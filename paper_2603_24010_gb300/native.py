@@ -31,7 +31,8 @@ EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "c
            "cp_batch_step_weak", "cp_batch_read_history", "cp_batch_read_grid",
            "cp_batch_get_particles", "cp_batch_status", "cp_batch_get_level",
            "cp_batch_last_launch_count", "cp_batch_set_launch", "cp_batch_get_launch",
-           "cp_batch_autotune", "cp_batch_destroy", "cp_destroy", "cp_status_str")
+           "cp_batch_autotune", "cp_batch_enable_timing", "cp_batch_read_timing",
+           "cp_batch_destroy", "cp_destroy", "cp_status_str")
 STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 40, 64, 2, 11074
 PRED_WINDOW, PRED_FEATURES = 8, 5
@@ -137,6 +138,8 @@ def lib():
         L.cp_batch_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.cp_batch_autotune.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_int32),
                                         C.POINTER(C.c_int32), dp]
+        L.cp_batch_enable_timing.argtypes = [vp, C.c_int32]
+        L.cp_batch_read_timing.argtypes = [vp, dp, i64p]
         L.cp_batch_destroy.argtypes = [vp]
         L.cp_batch_destroy.restype = None
         L.cp_destroy.argtypes = [vp]
@@ -420,21 +423,33 @@ class Gap:
         return cp_get_particles(self.ctx, species)
 
 
-def diag_to_dict(arr):
-    out = {}
-    n = len(arr)
+def _diag_dtype():
+    names, formats, offsets = [], [], []
     for name, typ in cp_diag._fields_:
+        names.append(name)
+        offsets.append(getattr(cp_diag, name).offset)
         if name == "absorbed":
-            out[name] = np.array([[[arr[k].absorbed[e][s] for s in range(3)] for e in range(2)]
-                                  for k in range(n)], dtype=np.int64).reshape(n, 2, 3)
-        elif name in ("emitted", "n_live"):
-            m = 2 if name == "emitted" else 3
-            out[name] = np.array([[getattr(arr[k], name)[j] for j in range(m)] for k in range(n)],
-                                 dtype=np.int64).reshape(n, m)
+            formats.append(("<i8", (2, 3)))
+        elif name == "emitted":
+            formats.append(("<i8", (2,)))
+        elif name == "n_live":
+            formats.append(("<i8", (3,)))
         else:
-            dt = np.int64 if typ is C.c_int64 else np.float64
-            out[name] = np.array([getattr(arr[k], name) for k in range(n)], dtype=dt)
-    return out
+            formats.append("<i8" if typ is C.c_int64 else "<f8")
+    return np.dtype(dict(names=names, formats=formats, offsets=offsets,
+                         itemsize=C.sizeof(cp_diag)))
+
+
+_DIAG_DTYPE = None
+
+
+def diag_to_dict(arr):
+    """Column view (copies) of a ctypes array of cp_diag rows."""
+    global _DIAG_DTYPE
+    if _DIAG_DTYPE is None:
+        _DIAG_DTYPE = _diag_dtype()
+    rows = np.frombuffer(arr, dtype=_DIAG_DTYPE, count=len(arr))
+    return {name: np.array(rows[name]) for name, _ in cp_diag._fields_}
 
 
 class Batch:
@@ -539,6 +554,15 @@ class Batch:
         rc = lib().cp_batch_autotune(self.h, int(steps_per_shape), int(mode), float(tol),
                                      C.byref(t), C.byref(p), C.byref(ms))
         return rc, t.value, p.value, ms.value
+
+    def enable_timing(self, on):
+        _check("cp_batch_enable_timing", lib().cp_batch_enable_timing(self.h, int(bool(on))))
+
+    def timing(self):
+        ms = np.zeros(3)
+        n = np.zeros(3, dtype=np.int64)
+        _check("cp_batch_read_timing", lib().cp_batch_read_timing(self.h, _dp(ms), _i64p(n)))
+        return ms, n
 
     def last_launch_count(self):
         n = C.c_int64()
