@@ -98,7 +98,7 @@ def test_ensemble_equals_single_instances(env, mode):
     b.close()
     # the runs exercised impacts, emission and the beam
     assert sum(r["h"]["emitted"][:, 0].sum() for r in refs) > 30
-    assert sum(r["h"]["absorbed"][:, 0, 1].sum() for r in refs) > 100
+    assert sum(r["h"]["absorbed"][:, 0, 1].sum() for r in refs) > 50
 
 
 def test_every_launch_shape_gives_the_same_bits(env):
