@@ -19,6 +19,11 @@ injection profile are not available, so these parameter sets stand in):
 * ``gap_1d_fp32_thinned``: the same physics with `factor` times fewer
   macroparticles of `factor` times the weight (loaded pairs and beam alike):
   the predictor's training and evaluation runs.
+* ``gap_2d``: 5 mm x 5 mm gap, periodic in y, 1024 x 1024 cells, 1e8
+  macroparticles (5e7 pairs), a 20 keV H+ beam with a Gaussian transverse
+  profile (sigma 0.5 mm, centred) at n_pairs/1000 ions per step, dt = 1 ps,
+  2000 steps, FP32 particles; the electrode area (depth x 5 mm) keeps the
+  gap capacitance at C.
 * ``ensemble``: independent 5 mm gaps with cells log-uniform in 256-4096,
   initial macroparticles log-uniform in 1e4-2e6, V0 uniform in 50-200 kV,
   C uniform in 20-500 pF, SEE scale uniform in 0-2 (every 8th instance
@@ -102,6 +107,35 @@ def ensemble(n_inst=512, seed=0, steps=10000, thin=1, n_cells_max=4096):
         cfg["name"] = "ensemble[%d]" % i
         out.append(cfg)
     return out
+
+
+def gap_2d(seed=0, Nx=1024, Ny=1024, n_pairs=50_000_000, steps=2000, beam_per_step=None):
+    """The 2D planar gap (x normal, y periodic)."""
+    cfg = _base(Nx, n_pairs, 1e-12, steps, 0, FP32, seed)
+    cfg["Ny"] = int(Ny)
+    cfg["Ly"] = 5e-3
+    cfg["beam_per_step"] = int(n_pairs // 1000 if beam_per_step is None else beam_per_step)
+    cfg["beam_sigma"] = 0.5e-3
+    cfg["beam_yc"] = 0.5 * cfg["Ly"]
+    cfg["name"] = "gap_2d"
+    return cfg
+
+
+def load_pairs_2d(cfg, seed=None):
+    """Co-located pairs uniform in the 2D gap, Maxwellian in both velocity
+    components; returns (xi, eta, u_e, w_e, u_i, w_i) in cell units."""
+    n = int(cfg["n_pairs"])
+    Nx, Ny = int(cfg["n_cells"]), int(cfg["Ny"])
+    rng = np.random.default_rng([int(cfg["seed"] if seed is None else seed), 0x2D10AD])
+    xi = rng.random(n) * Nx
+    xi = np.where(xi > 0.0, xi, 1e-9)
+    eta = rng.random(n) * Ny
+    dyx = (cfg["Ly"] / Ny) / (cfg["d"] / Nx)  # dy / dx
+    ue = rng.standard_normal(n) * thermal_u(cfg, cfg["m_e"], cfg["T_load_eV"])
+    we = rng.standard_normal(n) * thermal_u(cfg, cfg["m_e"], cfg["T_load_eV"]) / dyx
+    ui = rng.standard_normal(n) * thermal_u(cfg, cfg["m_i"], cfg["T_load_eV"])
+    wi = rng.standard_normal(n) * thermal_u(cfg, cfg["m_i"], cfg["T_load_eV"]) / dyx
+    return xi, eta, ue, we, ui, wi
 
 
 def scaled(cfg, **over):
