@@ -284,7 +284,7 @@ def run_ensemble(args, K, Wm):
     import torch
     from paper_2603_24010_gb300 import native
     n_inst = args.ensemble_instances
-    total = Wm + K + 1 + 5 * args.tune_steps
+    total = Wm + K + 1 + 5 * args.tune_steps + args.ensemble_timed_steps
     cfgs = W.ensemble(n_inst, seed=args.seed, steps=total)
     stream = torch.cuda.current_stream()
     loads = []
@@ -366,7 +366,7 @@ def ensemble_main(args, config):
                      "push_avg_ms": kms[0] / max(kn[0], 1), "solve_avg_ms": kms[1] / max(kn[1], 1),
                      "removal_avg_ms": kms[2] / max(kn[2], 1),
                      "source": "per-launch CUDA events over %d steps after the timed region"
-                               % kn[0]},
+                               % kn[0], "timed_steps": int(kn[0])},
         "clocks": st["clocks"],
         "autotuned_shape": st["shape"],
         "weak": {"value": r["weak"]["psteps"] / (r["weak"]["ms"] * 1e-3),

@@ -424,6 +424,62 @@ int cp_batch_autotune(cp_batch* b, int32_t steps_per_shape, int32_t mode, double
 
 void cp_batch_destroy(cp_batch* b);
 
+/* ------------------------------------------------------------------------
+ * 2D planar gap: x normal to the electrodes (as in the 1D gap), y periodic
+ * with n_cells_y cells over length_y.  The electrodes are equipotential
+ * planes of area A (cp_gap.area, or C d / eps0); the gap's depth is
+ * A / length_y.  Per step: gather of (E_x, E_y) by bilinear interpolation
+ * on the staggered grid, leapfrog push in both directions (y wraps),
+ * absorption and SEE at the electrodes (yield from the impact's kinetic
+ * energy; emitted electrons start at the impact's y, normal to the wall),
+ * beam ions entering at x = d with a Gaussian transverse profile
+ * (beam_sigma, centre beam_y0), bilinear fixed-point deposit (2^8 x 2^8 per
+ * macroparticle, end nodes in x doubled), and the solve: the transverse mean
+ * is the 1D coupled problem (strict or weak, with the circuit, exactly as
+ * cp_step_strict / cp_step_weak) and the other transverse Fourier modes
+ * solve tridiagonal systems in x with phi = 0 on both electrodes.  The
+ * particle store is kept sorted by 32 x 32-cell tiles, re-sorted every
+ * sort_every steps (0 => 8).  FP32 particles only; n_cells_y a power of two
+ * in 8..4096; n_cells <= 4096.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t n_cells_y;
+  int32_t sort_every;
+  double length_y;   /* [m] */
+  double beam_sigma; /* [m] */
+  double beam_y0;    /* [m] */
+} cp_transverse;
+
+typedef struct cp_gap2d cp_gap2d;
+
+int cp2d_create(const cp_gap* gap, const cp_transverse* tr, const cp_circuit* circuit,
+                const cp_see_beam* see, const cp_run* run, void* stream, cp_gap2d** out);
+/* Particles of one species before the first step: x, y, vx, vy (cell units
+   xi = x/dx, eta = y/dy, u = vx dt/dx, w = vy dt/dy, or SI), ids as in
+   cp_set_particles.  Errors: CP_ERR_ARG. */
+int cp2d_set_particles(cp_gap2d* g, int32_t species, const double* x, const double* y,
+                       const double* vx, const double* vy, const uint32_t* id, int64_t n,
+                       int32_t units);
+int cp2d_step_strict(cp_gap2d* g, int32_t n_steps, double residual_tol);
+int cp2d_step_weak(cp_gap2d* g, int32_t n_steps);
+/* Diagnostics rows (V_gap = phi on the driven electrode, circuit, tallies). */
+int cp2d_read_history(cp_gap2d* g, int64_t first, int64_t n, cp_diag* out);
+int cp2d_get_level(cp_gap2d* g, int64_t* level);
+/* Current fields, row-major over x: phi[(Nx+1) Ny], Ex[Nx Ny] at (i+1/2, j),
+   Ey[(Nx+1) Ny] at (i, j+1/2), and the charge grid G[(Nx+1) Ny] of the
+   level (2^16 per macroparticle).  Any pointer may be NULL. */
+int cp2d_read_fields(cp_gap2d* g, double* phi, float* Ex, float* Ey, int64_t* G);
+/* Live particles of one species (cell units); *n receives the count.
+   Errors: CP_ERR_CAPACITY if cap is too small. */
+int cp2d_get_particles(cp_gap2d* g, int32_t species, double* xi, double* eta, double* u, double* w,
+                       uint32_t* id, int64_t cap, int64_t* n);
+/* Per-kernel-group timing while on: ms[0] push, ms[1] solve (all its
+   kernels), ms[2] sort, and the number of each. */
+int cp2d_enable_timing(cp_gap2d* g, int32_t on);
+int cp2d_read_timing(cp_gap2d* g, double ms[3], int64_t n[3]);
+int cp2d_last_launch_count(cp_gap2d* g, int64_t* launches);
+void cp2d_destroy(cp_gap2d* g);
+
 void cp_destroy(cp_ctx* ctx);
 const char* cp_status_str(int status);
 

@@ -219,7 +219,8 @@ class Oracle2D:
                 w = q["w"] + f * self.ky[s] * ey
                 xi = q["xi"] + u
                 eta = q["eta"] + w
-                eta = np.where(eta >= Ny, eta - Ny, np.where(eta < 0, eta + Ny, eta))
+                eta = np.where(eta < 0, eta + Ny, eta)
+                eta = np.where(eta >= Ny, eta - Ny, eta)  # (a tiny negative value + Ny rounds to Ny)
                 gone0 = xi <= 0
                 gone1 = ~(xi > 0) | ~(xi < Nx)
                 gone1 = gone1 & ~gone0

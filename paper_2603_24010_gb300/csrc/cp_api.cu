@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "cp_device.cuh"
+#include "cp_gap2d.cuh"
 
 namespace cpk {
 size_t push_smem_bytes(int N, int precision);
@@ -42,6 +43,15 @@ cudaError_t solve_ens_configure(int precision, size_t smem);
 cudaError_t solve_ens_launch(int precision, const Bufs* Ball, int n_inst, size_t smem,
                              cudaStream_t st, int do_push, int mode, double tol);
 cudaError_t status_ens_launch(const Bufs* Ball, int E, int* out, cudaStream_t st);
+cudaError_t push2_occupancy(int* per_sm);
+cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* abs, int abs_cap,
+                         int grid, cudaStream_t st);
+cudaError_t sort2_launch(DevState* S, void* D, int T, int s, int sms, cudaStream_t st);
+cudaError_t solve2_fwd_launch(void* D, long long* G1, int Nx, int Ny, cudaStream_t st);
+cudaError_t solve2_modes_launch(void* D, int Nx, int Ny, float c_rhs, const double* E64,
+                                cudaStream_t st);
+cudaError_t deposit2_level0_launch(DevState* S, const void* D, int sms, cudaStream_t st);
+cudaError_t tables2_launch(void* D, int Ny, double r2, cudaStream_t st);
 cudaError_t samples_launch(const DevParams* P, const cp_diag* hist, int64_t first, int64_t n,
                            float* X, float* Y, cudaStream_t st);
 }  // namespace cpk
@@ -1275,6 +1285,475 @@ void cp_batch_destroy(cp_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_free(b);
   delete b;
+}
+
+// ---- 2D planar gap ------------------------------------------------------------
+}  // extern "C"
+
+struct cp_gap2d {
+  cp_ctx* c = nullptr;  // the 1D problem of the transverse mean (circuit, history)
+  int Nx = 0, Ny = 0, T = 0, sms = 0, grid = 0;
+  int sort_every = 8, since_sort = 0;
+  double ly = 0.0, beam_sigma = 0.0, beam_yc = 0.0;
+  bool initialized = false;
+  cpk::Dev2D hd{};             // host copy of the device struct
+  cpk::Dev2D* dD = nullptr;
+  void* abs = nullptr;
+  int abs_cap = 4096;
+  std::vector<double> hx[kSpecies], hy[kSpecies], hu[kSpecies], hw[kSpecies];
+  std::vector<uint32_t> hid;
+  std::vector<void*> owned;    // device allocations of this object
+  int64_t launches = 0;
+  bool timing = false;
+  double t_ms[3] = {0.0, 0.0, 0.0};  // push, solve (all kernels), sort
+  int64_t t_n[3] = {0, 0, 0};
+  std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+int g2_alloc(cp_gap2d* g, void** p, size_t bytes) {
+  CP_TRY(alloc(p, bytes));
+  g->owned.push_back(*p);
+  return CP_OK;
+}
+
+void g2_free(cp_gap2d* g) {
+  for (void* p : g->owned) cudaFree(p);
+  g->owned.clear();
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  g->ev.clear();
+  if (g->c) {
+    // the 1D context's particle pointers are this object's: forget them first
+    cp_ctx* c = g->c;
+    for (int b = 0; b < 2; ++b) {
+      for (int s = 0; s < kSpecies; ++s) c->buf_xi[b][s] = c->buf_u[b][s] = nullptr;
+      c->buf_id[b] = nullptr;
+    }
+    cp_destroy(c);
+    g->c = nullptr;
+  }
+}
+
+// Kernels of one step after the push: row sums + spectra, the 1D coupled
+// solve of the mean, the transverse modes and the fields.
+int g2_solve(cp_gap2d* g, int do_push, int mode, double tol) {
+  cp_ctx* c = g->c;
+  const cpk::Bufs B = make_bufs(c);
+  CP_CUDA(cpk::solve2_fwd_launch(g->dD, c->G, g->Nx, g->Ny, c->stream));
+  CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_ctas, c->solve_smem, c->stream, do_push, mode, tol));
+  const float c_rhs = static_cast<float>(-c->hp.dx * c->hp.dx / c->hp.eps0);
+  CP_CUDA(cpk::solve2_modes_launch(g->dD, g->Nx, g->Ny, c_rhs, c->E64, c->stream));
+  g->launches += 6;
+  return CP_OK;
+}
+
+int g2_sort(cp_gap2d* g) {
+  cp_ctx* c = g->c;
+  for (int s = 0; s < kSpecies; ++s) CP_CUDA(cpk::sort2_launch(c->dS, g->dD, g->T, s, g->sms, c->stream));
+  g->launches += 4 * kSpecies;
+  return CP_OK;
+}
+
+int g2_init(cp_gap2d* g, int mode, double tol) {
+  cp_ctx* c = g->c;
+  cpk::DevParams& P = c->hp;
+  int64_t n[kSpecies];
+  for (int s = 0; s < kSpecies; ++s) n[s] = static_cast<int64_t>(g->hx[s].size());
+  const int64_t Bm = P.beam_per_step;
+  const int64_t pad = 4 * static_cast<int64_t>(g->T) + 64;
+  const int64_t ions_ever = n[1] + Bm * c->max_steps;
+  const int64_t def[kSpecies] = {round4(n[0]) + pad, round4(ions_ever) + pad,
+                                 std::max<int64_t>(65536, round4(ions_ever + n[2]) + pad)};
+  for (int s = 0; s < kSpecies; ++s) {
+    c->cap[s] = round4(c->cap_req[s] > 0 ? std::max<int64_t>(c->cap_req[s], round4(n[s]) + pad) : def[s]);
+    P.cap[s] = c->cap[s];
+  }
+  cpk::Dev2D& D = g->hd;
+  // particle stores: x, u (the 1D state's buffers), y, w, ids; two of each
+  for (int b = 0; b < 2; ++b) {
+    for (int s = 0; s < kSpecies; ++s) {
+      void* bufs[4];
+      for (int k = 0; k < 4; ++k) CP_TRY(g2_alloc(g, &bufs[k], sizeof(float) * c->cap[s]));
+      CP_CUDA(cpk::fill_launch(CP_FP32, bufs[0], c->cap[s], -1.0, c->stream));
+      for (int k = 1; k < 4; ++k) CP_CUDA(cudaMemsetAsync(bufs[k], 0, sizeof(float) * c->cap[s], c->stream));
+      c->buf_xi[b][s] = bufs[0];
+      c->buf_u[b][s] = bufs[1];
+      (b == 0 ? D.y : D.y_alt)[s] = bufs[2];
+      (b == 0 ? D.w : D.w_alt)[s] = bufs[3];
+    }
+    void* idb = nullptr;
+    CP_TRY(g2_alloc(g, &idb, sizeof(uint32_t) * c->cap[1]));
+    c->buf_id[b] = static_cast<uint32_t*>(idb);
+  }
+  for (int s = 0; s < kSpecies; ++s) {
+    if (!n[s]) continue;
+    std::vector<float> f(n[s]);
+    const std::vector<double>* src[4] = {&g->hx[s], &g->hu[s], &g->hy[s], &g->hw[s]};
+    void* dst[4] = {c->buf_xi[0][s], c->buf_u[0][s], D.y[s], D.w[s]};
+    for (int k = 0; k < 4; ++k) {
+      for (int64_t q = 0; q < n[s]; ++q) f[q] = static_cast<float>((*src[k])[q]);
+      CP_CUDA(cudaMemcpyAsync(dst[k], f.data(), 4 * n[s], cudaMemcpyHostToDevice, c->stream));
+      CP_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  }
+  uint32_t id_base = 0;
+  if (n[1]) {
+    CP_CUDA(cudaMemcpyAsync(c->buf_id[0], g->hid.data(), 4 * n[1], cudaMemcpyHostToDevice, c->stream));
+    for (uint32_t v : g->hid) id_base = std::max<uint32_t>(id_base, v + 1u);
+  }
+  if (static_cast<double>(id_base) + static_cast<double>(Bm) * c->max_steps > 4294967295.0)
+    return CP_ERR_ARG;
+  // the 1D mean problem's grids, parameters and state
+  const int N = c->N;
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->G), sizeof(long long) * (N + 1)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->Glast), sizeof(long long) * (N + 1)));
+  CP_TRY(alloc(&c->Epair, 2 * sizeof(float) * (N + 1)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->phi), sizeof(double) * (N + 1)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->E64), sizeof(double) * N));
+  c->hist_rows = c->max_steps + 1;
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->hist), sizeof(cp_diag) * c->hist_rows));
+  CP_CUDA(cudaMemsetAsync(c->G, 0, sizeof(long long) * (N + 1), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->Glast, 0, sizeof(long long) * (N + 1), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->Epair, 0, 2 * sizeof(float) * (N + 1), c->stream));
+  CP_CUDA(cudaMemsetAsync(c->hist, 0, sizeof(cp_diag) * c->hist_rows, c->stream));
+  CP_CUDA(cpk::solve_cluster_size(c->precision, N, &c->solve_ctas));
+  c->solve_smem = cpk::solve_smem_bytes(N, c->solve_ctas);
+  CP_CUDA(cpk::solve_configure(c->precision, c->solve_smem));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->abs), sizeof(cpk::AbsRec)));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->dP), sizeof(cpk::DevParams)));
+  CP_CUDA(cudaMemcpyAsync(c->dP, &c->hp, sizeof(cpk::DevParams), cudaMemcpyHostToDevice, c->stream));
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->vs), sizeof(double) * (c->hist_rows + 1)));
+  CP_CUDA(cpk::source_table_launch(c->dP, c->vs, c->hist_rows + 1, c->stream));
+  cpk::DevState S;
+  std::memset(&S, 0, sizeof(S));
+  for (int s = 0; s < kSpecies; ++s) {
+    S.xi[s] = c->buf_xi[0][s];
+    S.u[s] = c->buf_u[0][s];
+    S.xi_alt[s] = c->buf_xi[1][s];
+    S.u_alt[s] = c->buf_u[1][s];
+    S.n_alloc[s] = round4(n[s]);
+    S.n_proc[s] = round4(n[s]);
+    S.n_live[s] = n[s];
+  }
+  S.id = c->buf_id[0];
+  S.id_alt = c->buf_id[1];
+  S.sigma = c->sigma0;
+  S.beam_id_base = id_base;
+  CP_TRY(alloc(reinterpret_cast<void**>(&c->dS), sizeof(cpk::DevState)));
+  CP_CUDA(cudaMemcpyAsync(c->dS, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  // 2D grids and tables
+  const int Nx = g->Nx, Ny = g->Ny, M = Ny / 2 + 1, T = g->T;
+  const size_t nodes = static_cast<size_t>(Nx + 1) * Ny;
+  void* p = nullptr;
+  CP_TRY(g2_alloc(g, &p, sizeof(int) * 3 * (T + 1))); D.tile_start = static_cast<int*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(int) * 3 * (T + 1))); D.wi_off = static_cast<int*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(int) * 3 * T)); D.tile_cnt = static_cast<int*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(int) * 3 * T)); D.tile_cur = static_cast<int*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float) * Nx * Ny)); D.Ex = static_cast<float*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float) * nodes)); D.Ey = static_cast<float*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(long long) * nodes)); D.G2 = static_cast<long long*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(long long) * nodes)); D.G2last = static_cast<long long*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float2) * (Nx + 1) * M)); D.R = static_cast<float2*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float) * (Nx + 1) * M)); D.cp = static_cast<float*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float) * nodes)); D.phit = static_cast<float*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float) * M)); D.kappa = static_cast<float*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float2) * (Ny / 2))); D.tw = static_cast<float2*>(p);
+  for (int* q : {D.tile_start, D.wi_off}) CP_CUDA(cudaMemsetAsync(q, 0, sizeof(int) * 3 * (T + 1), c->stream));
+  for (int* q : {D.tile_cnt, D.tile_cur}) CP_CUDA(cudaMemsetAsync(q, 0, sizeof(int) * 3 * T, c->stream));
+  CP_CUDA(cudaMemsetAsync(D.G2, 0, sizeof(long long) * nodes, c->stream));
+  CP_CUDA(cudaMemsetAsync(D.G2last, 0, sizeof(long long) * nodes, c->stream));
+  CP_CUDA(cudaMemsetAsync(D.phit, 0, sizeof(float) * nodes, c->stream));
+  CP_CUDA(cudaMemsetAsync(D.R, 0, sizeof(float2) * (Nx + 1) * M, c->stream));
+  D.Nx = Nx;
+  D.Ny = Ny;
+  D.ntx = (Nx + cpk::kT2 - 1) / cpk::kT2;
+  D.nty = (Ny + cpk::kT2 - 1) / cpk::kT2;
+  D.T = T;
+  D.sort_every = g->sort_every;
+  D.Nxf = static_cast<float>(Nx);
+  D.Nyf = static_cast<float>(Ny);
+  D.dx = P.dx;
+  D.dy = g->ly / Ny;
+  D.inv_dx = static_cast<float>(1.0 / D.dx);
+  D.inv_dy = static_cast<float>(1.0 / D.dy);
+  const double Lz = P.area / g->ly;
+  D.rho_scale = P.e * P.weight / (D.dx * D.dy * Lz * cpk::kFix);
+  const double dt = P.dt;
+  const double q_m[kSpecies] = {-P.e / P.m_e, P.e / P.m_i, -P.e / P.m_e};
+  for (int s = 0; s < kSpecies; ++s) {
+    const double kx = q_m[s] * dt * dt / D.dx, ky = q_m[s] * dt * dt / D.dy;
+    D.kx[0][s] = static_cast<float>(0.5 * kx);
+    D.kx[1][s] = static_cast<float>(kx);
+    D.ky[0][s] = static_cast<float>(0.5 * ky);
+    D.ky[1][s] = static_cast<float>(ky);
+  }
+  D.beam_sigma = g->beam_sigma / D.dy;
+  D.beam_yc = g->beam_yc / D.dy;
+  int lg = 0;
+  while ((1 << lg) < Ny) ++lg;
+  D.logNy = lg;
+  D.use_win = (Ny >= cpk::kW2) ? 1 : 0;
+  for (int s = 0; s < kSpecies; ++s) D.n_sorted[s] = 0;
+  CP_TRY(g2_alloc(g, reinterpret_cast<void**>(&g->dD), sizeof(cpk::Dev2D)));
+  CP_CUDA(cudaMemcpyAsync(g->dD, &D, sizeof(D), cudaMemcpyHostToDevice, c->stream));
+  CP_CUDA(cpk::tables2_launch(g->dD, Ny, (D.dx / D.dy) * (D.dx / D.dy), c->stream));
+  int per_sm = 0;
+  CP_CUDA(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, c->device));
+  CP_CUDA(cpk::push2_occupancy(&per_sm));
+  if (per_sm < 1) return CP_ERR_ARG;
+  g->grid = per_sm * g->sms;
+  CP_TRY(g2_alloc(g, &g->abs, sizeof(cpk::AbsRec2) * static_cast<size_t>(g->grid) * g->abs_cap));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < kSpecies; ++s) {
+    std::vector<double>().swap(g->hx[s]);
+    std::vector<double>().swap(g->hy[s]);
+    std::vector<double>().swap(g->hu[s]);
+    std::vector<double>().swap(g->hw[s]);
+  }
+  c->initialized = true;
+  g->initialized = true;
+  // level 0: sort, deposit, solve
+  CP_TRY(g2_sort(g));
+  g->since_sort = 0;
+  CP_CUDA(cpk::deposit2_level0_launch(c->dS, g->dD, g->sms, c->stream));
+  CP_TRY(g2_solve(g, 0, mode, tol));
+  return CP_OK;
+}
+
+int g2_timed(cp_gap2d* g, int which, std::vector<std::pair<int, size_t>>* rec) {
+  const size_t k = rec->size() * 2;
+  while (g->ev.size() < k + 2) {
+    cudaEvent_t e;
+    CP_CUDA(cudaEventCreate(&e));
+    g->ev.push_back(e);
+  }
+  CP_CUDA(cudaEventRecord(g->ev[k], g->c->stream));
+  rec->push_back({which, k});
+  return CP_OK;
+}
+
+int g2_steps(cp_gap2d* g, int mode, int32_t n_steps, double tol) {
+  if (!g || n_steps < 0 || !(tol > 0.0)) return CP_ERR_ARG;
+  cp_ctx* c = g->c;
+  CP_CUDA(cudaSetDevice(c->device));
+  g->launches = 0;
+  if (!g->initialized) CP_TRY(g2_init(g, mode, tol));
+  int64_t level = 0;
+  CP_CUDA(cudaMemcpyAsync(&level, &c->dS->level, sizeof(level), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  if (level + n_steps > c->max_steps) return CP_ERR_ARG;
+  std::vector<std::pair<int, size_t>> rec;
+  auto mark_end = [&](void) -> int {
+    const size_t k = rec.back().second;
+    CP_CUDA(cudaEventRecord(g->ev[k + 1], c->stream));
+    return CP_OK;
+  };
+  for (int k = 0; k < n_steps; ++k) {
+    if (g->since_sort == g->sort_every) {  // periodic re-sort (also drops absorbed slots)
+      if (g->timing) CP_TRY(g2_timed(g, 2, &rec));
+      CP_TRY(g2_sort(g));
+      if (g->timing) CP_TRY(mark_end());
+      g->since_sort = 0;
+    }
+    if (g->timing) CP_TRY(g2_timed(g, 0, &rec));
+    CP_CUDA(cpk::push2_launch(c->dP, c->dS, g->dD, g->abs, g->abs_cap, g->grid, c->stream));
+    g->launches += 1;
+    if (g->timing) CP_TRY(mark_end());
+    if (g->timing) CP_TRY(g2_timed(g, 1, &rec));
+    CP_TRY(g2_solve(g, 1, mode, tol));
+    if (g->timing) CP_TRY(mark_end());
+    g->since_sort += 1;
+  }
+  if (g->timing) {
+    CP_CUDA(cudaStreamSynchronize(c->stream));
+    for (const auto& r : rec) {
+      float ms = 0.f;
+      CP_CUDA(cudaEventElapsedTime(&ms, g->ev[r.second], g->ev[r.second + 1]));
+      g->t_ms[r.first] += ms;
+      g->t_n[r.first] += 1;
+    }
+  }
+  return read_status(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cp2d_create(const cp_gap* gap, const cp_transverse* tr, const cp_circuit* circuit,
+                const cp_see_beam* see, const cp_run* run, void* stream, cp_gap2d** out) {
+  if (!out || !gap || !tr || !circuit || !see || !run) return CP_ERR_ARG;
+  *out = nullptr;
+  const int Ny = tr->n_cells_y;
+  if (run->precision != CP_FP32 || Ny < 8 || Ny > 4096 || (Ny & (Ny - 1)) != 0 ||
+      gap->n_cells > 4096 || !(tr->length_y > 0) || tr->sort_every < 0 || !(tr->beam_sigma >= 0))
+    return CP_ERR_ARG;
+  cp_gap2d* g = new (std::nothrow) cp_gap2d();
+  if (!g) return CP_ERR_OOM;
+  const int rc = cp_create(gap, circuit, see, run, stream, &g->c);
+  if (rc != CP_OK) {
+    delete g;
+    return rc;
+  }
+  g->c->ens_member = true;
+  g->Nx = gap->n_cells;
+  g->Ny = Ny;
+  g->T = ((g->Nx + cpk::kT2 - 1) / cpk::kT2) * ((Ny + cpk::kT2 - 1) / cpk::kT2);
+  g->ly = tr->length_y;
+  g->beam_sigma = tr->beam_sigma;
+  g->beam_yc = tr->beam_y0;
+  g->sort_every = tr->sort_every > 0 ? tr->sort_every : 8;
+  *out = g;
+  return CP_OK;
+}
+
+int cp2d_set_particles(cp_gap2d* g, int32_t species, const double* x, const double* y,
+                       const double* vx, const double* vy, const uint32_t* id, int64_t n,
+                       int32_t units) {
+  if (!g || species < 0 || species >= kSpecies || n < 0 || g->initialized ||
+      (units != CP_UNITS_CELL && units != CP_UNITS_SI) || (n > 0 && (!x || !y || !vx || !vy)))
+    return CP_ERR_ARG;
+  const double dx = g->c->hp.dx, dy = g->ly / g->Ny, dt = g->c->hp.dt;
+  const float Nx = static_cast<float>(g->Nx), Ny = static_cast<float>(g->Ny);
+  std::vector<double> hx(n), hy(n), hu(n), hw(n);
+  for (int64_t k = 0; k < n; ++k) {
+    const double xi = units == CP_UNITS_SI ? x[k] / dx : x[k];
+    const double eta = units == CP_UNITS_SI ? y[k] / dy : y[k];
+    const double u = units == CP_UNITS_SI ? vx[k] * dt / dx : vx[k];
+    const double w = units == CP_UNITS_SI ? vy[k] * dt / dy : vy[k];
+    if (!(xi > 0.0) || !(xi < g->Nx) || !(eta >= 0.0) || !(eta < g->Ny) || !std::isfinite(u) ||
+        !std::isfinite(w))
+      return CP_ERR_ARG;
+    float fx = static_cast<float>(xi), fy = static_cast<float>(eta);
+    if (fx >= Nx) fx = std::nextafter(Nx, 0.0f);
+    if (!(fx > 0.0f)) fx = 1.17549435e-38f;
+    if (fy >= Ny) fy = 0.0f;
+    hx[k] = fx;
+    hy[k] = fy;
+    hu[k] = static_cast<float>(u);
+    hw[k] = static_cast<float>(w);
+  }
+  g->hx[species].swap(hx);
+  g->hy[species].swap(hy);
+  g->hu[species].swap(hu);
+  g->hw[species].swap(hw);
+  if (species == CP_IONS) {
+    g->hid.resize(n);
+    for (int64_t k = 0; k < n; ++k) g->hid[k] = id ? id[k] : static_cast<uint32_t>(k);
+  }
+  return CP_OK;
+}
+
+int cp2d_step_strict(cp_gap2d* g, int32_t n_steps, double residual_tol) {
+  return g2_steps(g, 0, n_steps, residual_tol);
+}
+
+int cp2d_step_weak(cp_gap2d* g, int32_t n_steps) { return g2_steps(g, 1, n_steps, 1e300); }
+
+int cp2d_read_history(cp_gap2d* g, int64_t first, int64_t n, cp_diag* out) {
+  if (!g) return CP_ERR_ARG;
+  return cp_read_history(g->c, first, n, out);
+}
+
+int cp2d_get_level(cp_gap2d* g, int64_t* level) {
+  if (!g) return CP_ERR_ARG;
+  return cp_get_level(g->c, level);
+}
+
+int cp2d_read_fields(cp_gap2d* g, double* phi, float* Ex, float* Ey, int64_t* G) {
+  if (!g || !g->initialized) return CP_ERR_ARG;
+  cp_ctx* c = g->c;
+  CP_CUDA(cudaSetDevice(c->device));
+  const int Nx = g->Nx, Ny = g->Ny;
+  const size_t nodes = static_cast<size_t>(Nx + 1) * Ny;
+  if (phi) {
+    std::vector<double> p0(Nx + 1);
+    std::vector<float> pt(nodes);
+    CP_CUDA(cudaMemcpyAsync(p0.data(), c->phi, sizeof(double) * (Nx + 1), cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaMemcpyAsync(pt.data(), g->hd.phit, sizeof(float) * nodes, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i <= Nx; ++i)
+      for (int j = 0; j < Ny; ++j) phi[static_cast<size_t>(i) * Ny + j] = p0[i] + pt[static_cast<size_t>(i) * Ny + j];
+  }
+  if (Ex) CP_CUDA(cudaMemcpyAsync(Ex, g->hd.Ex, sizeof(float) * Nx * Ny, cudaMemcpyDeviceToHost, c->stream));
+  if (Ey) CP_CUDA(cudaMemcpyAsync(Ey, g->hd.Ey, sizeof(float) * nodes, cudaMemcpyDeviceToHost, c->stream));
+  if (G) CP_CUDA(cudaMemcpyAsync(G, g->hd.G2last, sizeof(long long) * nodes, cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  return CP_OK;
+}
+
+int cp2d_get_particles(cp_gap2d* g, int32_t species, double* xi, double* eta, double* u, double* w,
+                       uint32_t* id, int64_t cap, int64_t* n) {
+  if (!g || species < 0 || species >= kSpecies || !n || !g->initialized) return CP_ERR_ARG;
+  cp_ctx* c = g->c;
+  CP_CUDA(cudaSetDevice(c->device));
+  cpk::DevState S;
+  cpk::Dev2D D;
+  CP_CUDA(cudaMemcpyAsync(&S, c->dS, sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaMemcpyAsync(&D, g->dD, sizeof(D), cudaMemcpyDeviceToHost, c->stream));
+  CP_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t slots = std::min<int64_t>(S.n_alloc[species], c->cap[species]);
+  std::vector<float> hx(slots), hy(slots), hu(slots), hw(slots);
+  std::vector<uint32_t> hid(species == CP_IONS ? slots : 0);
+  if (slots > 0) {
+    CP_CUDA(cudaMemcpyAsync(hx.data(), S.xi[species], 4 * slots, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaMemcpyAsync(hu.data(), S.u[species], 4 * slots, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaMemcpyAsync(hy.data(), D.y[species], 4 * slots, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaMemcpyAsync(hw.data(), D.w[species], 4 * slots, cudaMemcpyDeviceToHost, c->stream));
+    if (species == CP_IONS)
+      CP_CUDA(cudaMemcpyAsync(hid.data(), S.id, 4 * slots, cudaMemcpyDeviceToHost, c->stream));
+    CP_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  int64_t m = 0;
+  for (int64_t k = 0; k < slots; ++k) {
+    if (!(hx[k] > 0.0f && hx[k] < static_cast<float>(g->Nx))) continue;
+    if (m < cap) {
+      if (xi) xi[m] = hx[k];
+      if (eta) eta[m] = hy[k];
+      if (u) u[m] = hu[k];
+      if (w) w[m] = hw[k];
+      if (id && species == CP_IONS) id[m] = hid[k];
+    }
+    ++m;
+  }
+  *n = m;
+  return m > cap ? CP_ERR_CAPACITY : CP_OK;
+}
+
+int cp2d_enable_timing(cp_gap2d* g, int32_t on) {
+  if (!g) return CP_ERR_ARG;
+  g->timing = (on != 0);
+  for (int k = 0; k < 3; ++k) {
+    g->t_ms[k] = 0.0;
+    g->t_n[k] = 0;
+  }
+  return CP_OK;
+}
+
+int cp2d_read_timing(cp_gap2d* g, double ms[3], int64_t n[3]) {
+  if (!g || !ms || !n) return CP_ERR_ARG;
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = g->t_ms[k];
+    n[k] = g->t_n[k];
+  }
+  return CP_OK;
+}
+
+int cp2d_last_launch_count(cp_gap2d* g, int64_t* launches) {
+  if (!g || !launches) return CP_ERR_ARG;
+  *launches = g->launches;
+  return CP_OK;
+}
+
+void cp2d_destroy(cp_gap2d* g) {
+  if (!g) return;
+  if (g->c) {
+    cudaSetDevice(g->c->device);
+    if (g->c->stream) cudaStreamSynchronize(g->c->stream);
+  }
+  g2_free(g);
+  delete g;
 }
 
 }  // extern "C"
