@@ -32,7 +32,10 @@ EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "c
            "cp_batch_get_particles", "cp_batch_status", "cp_batch_get_level",
            "cp_batch_last_launch_count", "cp_batch_set_launch", "cp_batch_get_launch",
            "cp_batch_autotune", "cp_batch_enable_timing", "cp_batch_read_timing",
-           "cp_batch_destroy", "cp_destroy", "cp_status_str")
+           "cp_batch_destroy", "cp2d_create", "cp2d_set_particles", "cp2d_step_strict",
+           "cp2d_step_weak", "cp2d_read_history", "cp2d_get_level", "cp2d_read_fields",
+           "cp2d_get_particles", "cp2d_enable_timing", "cp2d_read_timing", "cp2d_last_launch_count",
+           "cp2d_destroy", "cp_destroy", "cp_status_str")
 STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 40, 64, 2, 11074
 PRED_WINDOW, PRED_FEATURES = 8, 5
@@ -72,6 +75,11 @@ class cp_diag(C.Structure):
         "ion_energy_eV", "max_cfl", "J_hat")] + [
         ("absorbed", (C.c_int64 * 3) * 2), ("emitted", C.c_int64 * 2), ("injected", C.c_int64),
         ("n_live", C.c_int64 * 3), ("conv_count", C.c_int64)]
+
+
+class cp_transverse(C.Structure):
+    _fields_ = [("n_cells_y", C.c_int32), ("sort_every", C.c_int32), ("length_y", C.c_double),
+                ("beam_sigma", C.c_double), ("beam_y0", C.c_double)]
 
 
 class cp_predictor(C.Structure):
@@ -142,6 +150,20 @@ def lib():
         L.cp_batch_read_timing.argtypes = [vp, dp, i64p]
         L.cp_batch_destroy.argtypes = [vp]
         L.cp_batch_destroy.restype = None
+        L.cp2d_create.argtypes = [C.POINTER(cp_gap), C.POINTER(cp_transverse), C.POINTER(cp_circuit),
+                                  C.POINTER(cp_see_beam), C.POINTER(cp_run), vp, C.POINTER(vp)]
+        L.cp2d_set_particles.argtypes = [vp, C.c_int32, dp, dp, dp, dp, u32p, C.c_int64, C.c_int32]
+        L.cp2d_step_strict.argtypes = [vp, C.c_int32, C.c_double]
+        L.cp2d_step_weak.argtypes = [vp, C.c_int32]
+        L.cp2d_read_history.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(cp_diag)]
+        L.cp2d_get_level.argtypes = [vp, i64p]
+        L.cp2d_read_fields.argtypes = [vp, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), i64p]
+        L.cp2d_get_particles.argtypes = [vp, C.c_int32, dp, dp, dp, dp, u32p, C.c_int64, i64p]
+        L.cp2d_enable_timing.argtypes = [vp, C.c_int32]
+        L.cp2d_read_timing.argtypes = [vp, dp, i64p]
+        L.cp2d_last_launch_count.argtypes = [vp, i64p]
+        L.cp2d_destroy.argtypes = [vp]
+        L.cp2d_destroy.restype = None
         L.cp_destroy.argtypes = [vp]
         L.cp_destroy.restype = None
         L.cp_status_str.argtypes = [C.c_int]
@@ -567,4 +589,103 @@ class Batch:
     def last_launch_count(self):
         n = C.c_int64()
         _check("cp_batch_last_launch_count", lib().cp_batch_last_launch_count(self.h, C.byref(n)))
+        return n.value
+
+
+class Gap2D:
+    """The 2D planar gap (x normal, y periodic) driven through the cp2d_* calls."""
+
+    def __init__(self, cfg, max_steps=None, sort_every=0, capacity=(0, 0, 0), stream=None):
+        self.cfg = dict(cfg)
+        self.Nx, self.Ny = int(cfg["n_cells"]), int(cfg["Ny"])
+        gap, circ, see, run = structs_from_config(cfg, capacity=capacity, max_steps=max_steps)
+        tr = cp_transverse(n_cells_y=self.Ny, sort_every=int(sort_every), length_y=cfg["Ly"],
+                           beam_sigma=cfg["beam_sigma"], beam_y0=cfg["beam_yc"])
+        h = C.c_void_p()
+        _check("cp2d_create", lib().cp2d_create(C.byref(gap), C.byref(tr), C.byref(circ),
+                                                C.byref(see), C.byref(run),
+                                                C.c_void_p(current_stream() if stream is None else stream),
+                                                C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cp2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, species, xi, eta, u, w, ids=None, units=UNITS_CELL):
+        a = [np.ascontiguousarray(v, dtype=np.float64) for v in (xi, eta, u, w)]
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        _check("cp2d_set_particles", lib().cp2d_set_particles(
+            self.h, int(species), _dp(a[0]), _dp(a[1]), _dp(a[2]), _dp(a[3]), _u32p(ids),
+            a[0].size, int(units)))
+
+    def step(self, mode, n_steps, tol=1e-12):
+        if mode == STRICT:
+            rc = lib().cp2d_step_strict(self.h, int(n_steps), float(tol))
+        elif mode == WEAK:
+            rc = lib().cp2d_step_weak(self.h, int(n_steps))
+        else:
+            raise ValueError("the 2D gap runs strict or weak coupling")
+        _check("cp2d_step", rc)
+
+    @property
+    def level(self):
+        lv = C.c_int64()
+        _check("cp2d_get_level", lib().cp2d_get_level(self.h, C.byref(lv)))
+        return lv.value
+
+    def history(self, first=0, n=None):
+        if n is None:
+            n = self.level + 1 - first
+        arr = (cp_diag * int(n))()
+        _check("cp2d_read_history", lib().cp2d_read_history(self.h, int(first), int(n), arr))
+        return diag_to_dict(arr)
+
+    def fields(self):
+        Nx, Ny = self.Nx, self.Ny
+        phi = np.zeros((Nx + 1) * Ny)
+        Ex = np.zeros(Nx * Ny, dtype=np.float32)
+        Ey = np.zeros((Nx + 1) * Ny, dtype=np.float32)
+        G = np.zeros((Nx + 1) * Ny, dtype=np.int64)
+        fp = C.POINTER(C.c_float)
+        _check("cp2d_read_fields", lib().cp2d_read_fields(
+            self.h, _dp(phi), Ex.ctypes.data_as(fp), Ey.ctypes.data_as(fp), _i64p(G)))
+        return dict(phi=phi.reshape(Nx + 1, Ny), Ex=Ex.reshape(Nx, Ny), Ey=Ey.reshape(Nx + 1, Ny),
+                    G=G.reshape(Nx + 1, Ny))
+
+    def particles(self, species):
+        n = C.c_int64()
+        rc = lib().cp2d_get_particles(self.h, int(species), None, None, None, None, None, 0,
+                                      C.byref(n))
+        if rc not in (OK, ERR_CAPACITY):
+            _check("cp2d_get_particles", rc)
+        cap = max(n.value, 1)
+        a = [np.zeros(cap) for _ in range(4)]
+        ids = np.zeros(cap, dtype=np.uint32)
+        _check("cp2d_get_particles", lib().cp2d_get_particles(
+            self.h, int(species), _dp(a[0]), _dp(a[1]), _dp(a[2]), _dp(a[3]), _u32p(ids), cap,
+            C.byref(n)))
+        m = n.value
+        return [v[:m] for v in a] + [ids[:m] if species == IONS else None]
+
+    def enable_timing(self, on):
+        _check("cp2d_enable_timing", lib().cp2d_enable_timing(self.h, int(bool(on))))
+
+    def timing(self):
+        ms = np.zeros(3)
+        n = np.zeros(3, dtype=np.int64)
+        _check("cp2d_read_timing", lib().cp2d_read_timing(self.h, _dp(ms), _i64p(n)))
+        return ms, n
+
+    def last_launch_count(self):
+        n = C.c_int64()
+        _check("cp2d_last_launch_count", lib().cp2d_last_launch_count(self.h, C.byref(n)))
         return n.value

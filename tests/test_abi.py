@@ -19,7 +19,7 @@ def declared_functions():
             continue
         text = open(os.path.join(INCLUDE, f)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(cp_[a-z0-9_]+)\s*\(",
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(cp(?:2d)?_[a-z0-9_]+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names

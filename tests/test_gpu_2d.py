@@ -1,0 +1,156 @@
+"""The 2D planar gap on the GPU against the 2D oracle.
+
+* The bilinear fixed-point deposit is bit-exact on identical particle sets
+  (window path with several work items per tile, and the global path on a
+  grid too narrow for windows).
+* The level-0 fields equal the oracle's transverse-FFT solve (FP32 modes
+  around the FP64 mean).
+* One push from identical states agrees to FP32 rounding; a coupled run with
+  beam and SEE tracks the oracle's V_gap and circuit charge.
+* Results do not depend on how often the store is re-sorted (window and
+  global paths share their arithmetic), and a full-size step keeps the
+  charge and particle ledgers exact.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_24010_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_24010_gb300 import native
+    from oracle import gap2d
+    native.lib()
+    return torch, native, gap2d
+
+
+def f32(a):
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
+def loaded(cfg):
+    xi, eta, ue, we, ui, wi = W.load_pairs_2d(cfg)
+    xi = np.minimum(f32(xi), np.nextafter(np.float32(cfg["n_cells"]), np.float32(0)))
+    eta = f32(eta)
+    eta = np.where(eta >= cfg["Ny"], 0.0, eta)
+    return xi, eta, f32(ue), f32(we), f32(ui), f32(wi)
+
+
+def gpu_gap(native, cfg, steps, mode=0, sort_every=0, parts=None):
+    g = native.Gap2D(cfg, max_steps=max(steps, 1), sort_every=sort_every)
+    xi, eta, ue, we, ui, wi = parts if parts is not None else loaded(cfg)
+    g.set_particles(native.ELECTRONS, xi, eta, ue, we)
+    g.set_particles(native.IONS, xi, eta, ui, wi, np.arange(xi.size, dtype=np.uint32))
+    g.step(mode, steps)
+    return g
+
+
+def oracle_gap(gap2d, cfg, steps, mode=0, parts=None):
+    o = gap2d.Oracle2D(cfg)
+    xi, eta, ue, we, ui, wi = parts if parts is not None else loaded(cfg)
+    o.set_particles(0, xi, eta, ue, we)
+    o.set_particles(1, xi, eta, ui, wi)
+    assert o.step(mode, steps) == 0
+    return o
+
+
+def cfg2d(Nx, Ny, n_pairs, beam=0, gap=5e-3, see=1.0):
+    cfg = W.gap_2d(0, Nx=Nx, Ny=Ny, n_pairs=n_pairs, steps=10, beam_per_step=beam)
+    cfg["d"] = cfg["Ly"] = gap
+    cfg["area"] = cfg["C"] * cfg["d"] / cfg["eps0"]
+    cfg["weight"] = cfg["n0"] * cfg["d"] * cfg["area"] / cfg["n_pairs"]
+    cfg["beam_yc"], cfg["beam_sigma"] = gap / 2, gap / 10
+    cfg["see_scale"] = see
+    return cfg
+
+
+@pytest.mark.parametrize("Nx,Ny,n_pairs", [(64, 64, 150000), (96, 128, 40000), (40, 8, 20000)])
+def test_level0_deposit_and_fields(env, Nx, Ny, n_pairs):
+    torch, native, gap2d = env
+    cfg = cfg2d(Nx, Ny, n_pairs)
+    parts = loaded(cfg)
+    g = gpu_gap(native, cfg, 0, parts=parts)
+    f = g.fields()
+    g.close()
+    o = oracle_gap(gap2d, cfg, 0, parts=parts)
+    np.testing.assert_array_equal(f["G"], o.G)
+    scale = np.abs(o.phi).max()
+    np.testing.assert_allclose(f["phi"], o.phi, rtol=0, atol=2e-5 * scale)
+    ex_s = np.abs(o.Ex).max()
+    np.testing.assert_allclose(f["Ex"], o.Ex, rtol=0, atol=2e-4 * ex_s)
+    np.testing.assert_allclose(f["Ey"], o.Ey, rtol=0, atol=2e-4 * ex_s)
+
+
+def test_one_push_matches_the_oracle(env):
+    torch, native, gap2d = env
+    cfg = cfg2d(64, 64, 30000)
+    parts = loaded(cfg)
+    g = gpu_gap(native, cfg, 1, parts=parts)
+    o = oracle_gap(gap2d, cfg, 1, parts=parts)
+    for s in (native.ELECTRONS, native.IONS):
+        xg, yg, ug, wg, _ = g.particles(s)
+        q = o.p[s]
+        og, oo = np.lexsort((yg, xg)), np.lexsort((q["eta"], q["xi"]))
+        assert xg.size == q["xi"].size
+        np.testing.assert_allclose(xg[og], q["xi"][oo], rtol=0, atol=2e-4)
+        np.testing.assert_allclose(ug[og], q["u"][oo], rtol=1e-4, atol=1e-7 * np.abs(q["u"]).max())
+    hg, ho = g.history(), o.history()
+    np.testing.assert_allclose(hg["V_gap"], ho["V_gap"], rtol=1e-4, atol=1e-6 * np.abs(ho["V_gap"]).max())
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_coupled_run_tracks_the_oracle(env, mode):
+    torch, native, gap2d = env
+    cfg = cfg2d(64, 64, 8000, beam=24, gap=5e-4, see=8.0)
+    steps = 300
+    g = gpu_gap(native, cfg, steps, mode=mode)
+    hg = g.history()
+    g.close()
+    o = oracle_gap(gap2d, cfg, steps, mode=mode)
+    ho = o.history()
+    assert ho["absorbed"][:, 0, 1].sum() > 20 and ho["emitted"][:, 0].sum() > 5
+    for k in ("V_gap", "Q_surf", "Q_circ"):
+        scale = np.abs(ho[k]).max()
+        np.testing.assert_allclose(hg[k], ho[k], rtol=0, atol=5e-3 * scale, err_msg=k)
+
+
+def test_results_do_not_depend_on_the_sort_interval(env):
+    torch, native, gap2d = env
+    cfg = cfg2d(64, 64, 60000, beam=40, gap=5e-4, see=4.0)
+    steps = 40
+    parts = loaded(cfg)
+    hs = []
+    for every in (1, 3, 8):
+        g = gpu_gap(native, cfg, steps, sort_every=every, parts=parts)
+        hs.append((g.history(), g.fields()["G"]))
+        g.close()
+    for h, G in hs[1:]:
+        np.testing.assert_array_equal(h["V_gap"], hs[0][0]["V_gap"])
+        np.testing.assert_array_equal(h["n_live"], hs[0][0]["n_live"])
+        np.testing.assert_array_equal(G, hs[0][1])
+
+
+def test_full_size_ledgers(env):
+    torch, native, gap2d = env
+    cfg = W.gap_2d(0, n_pairs=20_000_000)
+    cfg["beam_per_step"] = 20000
+    parts = loaded(cfg)
+    steps = 12
+    g = gpu_gap(native, cfg, steps, parts=parts)
+    h = g.history()
+    G = g.fields()["G"].copy()
+    g.close()
+    nl = h["n_live"]
+    assert nl[0, 0] == 20_000_000
+    np.testing.assert_array_equal(np.diff(nl[:, 1]), -h["absorbed"][1:, :, 1].sum(axis=1) + 20000)
+    G[0] //= 2
+    G[-1] //= 2
+    assert G.sum() == 65536 * (nl[-1, 1] - nl[-1, 0] - nl[-1, 2])
+    assert np.all(h["residual"] <= 1e-12)
