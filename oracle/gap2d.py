@@ -221,6 +221,9 @@ class Oracle2D:
                 eta = q["eta"] + w
                 eta = np.where(eta < 0, eta + Ny, eta)
                 eta = np.where(eta >= Ny, eta - Ny, eta)  # (a tiny negative value + Ny rounds to Ny)
+                far = ~((eta >= 0) & (eta < Ny))  # more than one period in a step
+                eta = np.where(far, eta - Ny * np.floor(eta / Ny), eta)
+                eta = np.where((eta >= 0) & (eta < Ny), eta, 0.0)
                 gone0 = xi <= 0
                 gone1 = ~(xi > 0) | ~(xi < Nx)
                 gone1 = gone1 & ~gone0

@@ -1494,7 +1494,10 @@ int g2_init(cp_gap2d* g, int mode, double tol) {
   while ((1 << lg) < Ny) ++lg;
   D.logNy = lg;
   D.use_win = (Ny >= cpk::kW2) ? 1 : 0;
-  for (int s = 0; s < kSpecies; ++s) D.n_sorted[s] = 0;
+  for (int s = 0; s < kSpecies; ++s) {
+    D.n_sorted[s] = 0;
+    D.cap[s] = c->cap[s];
+  }
   CP_TRY(g2_alloc(g, reinterpret_cast<void**>(&g->dD), sizeof(cpk::Dev2D)));
   CP_CUDA(cudaMemcpyAsync(g->dD, &D, sizeof(D), cudaMemcpyHostToDevice, c->stream));
   CP_CUDA(cpk::tables2_launch(g->dD, Ny, (D.dx / D.dy) * (D.dx / D.dy), c->stream));

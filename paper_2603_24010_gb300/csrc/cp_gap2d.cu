@@ -254,6 +254,10 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
           float yn = yv[q] + wn;
           if (yn < 0.0f) yn += D.Nyf;
           if (yn >= D.Nyf) yn -= D.Nyf;
+          if (!(yn >= 0.0f && yn < D.Nyf)) {  // more than one period in a step (or not finite)
+            yn -= D.Nyf * floorf(yn / D.Nyf);
+            if (!(yn >= 0.0f && yn < D.Nyf)) yn = 0.0f;
+          }
           cfl = max(cfl, __float_as_uint(fmaxf(fabsf(un), fabsf(wn))));
           if (!(xn > 0.0f && xn < D.Nxf)) {  // absorbed
             const int el = (xn <= 0.0f) ? 0 : 1;
@@ -519,14 +523,17 @@ __global__ void k2_scan(DevState* S, Dev2D* Dp, int s) {
   int ra = ba + ia - a, rb = bb + ib - b;
   float* xd = reinterpret_cast<float*>(S->xi_alt[s]);
   float* ud = reinterpret_cast<float*>(S->u_alt[s]);
+  const long long cap = D.cap[s];
   for (int t = t0; t < t1; ++t) {
     ts[t] = ra;
     wo[t] = rb;
     cur[t] = ra;
     const int c = cnt[t], c4 = (c + 3) & ~3;
     for (int k = c; k < c4; ++k) {  // dead padding slots
-      xd[ra + k] = -1.0f;
-      ud[ra + k] = 0.0f;
+      if (ra + k < cap) {
+        xd[ra + k] = -1.0f;
+        ud[ra + k] = 0.0f;
+      }
     }
     ra += c4;
     rb += (c + kChunk2 - 1) / kChunk2;
@@ -579,6 +586,7 @@ __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
       if (tl[q] < 0) continue;
       const long long k = c0 + threadIdx.x + static_cast<long long>(q) * blockDim.x;
       const long long o = static_cast<long long>(loc[tl[q]]) + rank[q];
+      if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
       xd[o] = xs[k];
       ud[o] = us[k];
       yd[o] = ys[k];
@@ -602,7 +610,11 @@ __global__ void k2_swap(DevState* S, Dev2D* Dp, int s) {
     S->id = S->id_alt;
     S->id_alt = ti;
   }
-  const long long n = D.tile_start[s * (D.T + 1) + D.T];
+  long long n = D.tile_start[s * (D.T + 1) + D.T];
+  if (n > D.cap[s]) {
+    n = D.cap[s] & ~3LL;
+    atomicCAS(&S->status, 0, CP_ERR_CAPACITY);
+  }
   D.n_sorted[s] = n;
   S->n_alloc[s] = n;
   S->n_proc[s] = n;

@@ -29,6 +29,7 @@ struct Dev2D {
   void* y_alt[kSpecies];
   void* w_alt[kSpecies];
   long long n_sorted[kSpecies];
+  long long cap[kSpecies];  // slots of each store
   int* tile_start;  // [3][T+1] particle offsets of the sorted segments
   int* wi_off;      // [3][T+1] prefix of work items per tile
   int* tile_cnt;    // [3][T] live particles per tile (sort scratch)
