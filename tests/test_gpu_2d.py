@@ -93,13 +93,21 @@ def test_one_push_matches_the_oracle(env):
     parts = loaded(cfg)
     g = gpu_gap(native, cfg, 1, parts=parts)
     o = oracle_gap(gap2d, cfg, 1, parts=parts)
-    for s in (native.ELECTRONS, native.IONS):
-        xg, yg, ug, wg, _ = g.particles(s)
-        q = o.p[s]
-        og, oo = np.lexsort((yg, xg)), np.lexsort((q["eta"], q["xi"]))
-        assert xg.size == q["xi"].size
-        np.testing.assert_allclose(xg[og], q["xi"][oo], rtol=0, atol=2e-4)
-        np.testing.assert_allclose(ug[og], q["u"][oo], rtol=1e-4, atol=1e-7 * np.abs(q["u"]).max())
+    # ions are matched by id
+    xg, yg, ug, wg, ids = g.particles(native.IONS)
+    q = o.p[native.IONS]
+    og, oo = np.argsort(ids), np.argsort(o.ids)
+    np.testing.assert_array_equal(ids[og], o.ids[oo].astype(np.uint32))
+    for a_, b_, tol in ((xg, q["xi"], 2e-5), (yg, q["eta"], 2e-5), (ug, q["u"], 1e-6),
+                        (wg, q["w"], 1e-6)):
+        np.testing.assert_allclose(a_[og], b_[oo], rtol=0, atol=tol * max(1.0, np.abs(b_).max()))
+    # electrons (no ids): each coordinate's sorted values
+    xg, yg, ug, wg, _ = g.particles(native.ELECTRONS)
+    q = o.p[native.ELECTRONS]
+    assert xg.size == q["xi"].size
+    for a_, b_ in ((xg, q["xi"]), (yg, q["eta"]), (ug, q["u"]), (wg, q["w"])):
+        np.testing.assert_allclose(np.sort(a_), np.sort(b_), rtol=0,
+                                   atol=2e-5 * max(1.0, np.abs(b_).max()))
     hg, ho = g.history(), o.history()
     np.testing.assert_allclose(hg["V_gap"], ho["V_gap"], rtol=1e-4, atol=1e-6 * np.abs(ho["V_gap"]).max())
     g.close()
