@@ -111,7 +111,8 @@ def test_one_push_matches_the_oracle(env):
     # the grids of level 1 differ only where an FP32 position crossed a 1/256-cell
     # weight boundary: same total, nearly all nodes equal
     G = g.fields()["G"]
-    assert G.sum() == o.G.sum()
+    half = lambda a: np.concatenate([a[:1] // 2, a[1:-1], a[-1:] // 2])  # noqa: E731
+    assert half(G).sum() == half(o.G).sum()  # 2^16 per macroparticle on both sides
     assert (G != o.G).mean() < 0.02
     g.close()
 
