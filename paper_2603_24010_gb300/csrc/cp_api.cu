@@ -1351,7 +1351,7 @@ int g2_solve(cp_gap2d* g, int do_push, int mode, double tol) {
 int g2_sort(cp_gap2d* g) {
   cp_ctx* c = g->c;
   for (int s = 0; s < kSpecies; ++s) CP_CUDA(cpk::sort2_launch(c->dS, g->dD, g->T, s, g->sms, c->stream));
-  g->launches += 4 * kSpecies;
+  g->launches += 6 * kSpecies;
   return CP_OK;
 }
 
@@ -1456,6 +1456,7 @@ int g2_init(cp_gap2d* g, int mode, double tol) {
   CP_TRY(g2_alloc(g, &p, sizeof(long long) * nodes)); D.G2last = static_cast<long long*>(p);
   CP_TRY(g2_alloc(g, &p, sizeof(float2) * (Nx + 1) * M)); D.R = static_cast<float2*>(p);
   CP_TRY(g2_alloc(g, &p, sizeof(float) * (Nx + 1) * M)); D.cp = static_cast<float*>(p);
+  CP_TRY(g2_alloc(g, &p, sizeof(float) * (Nx + 1) * M)); D.tinv = static_cast<float*>(p);
   CP_TRY(g2_alloc(g, &p, sizeof(float) * nodes)); D.phit = static_cast<float*>(p);
   CP_TRY(g2_alloc(g, &p, sizeof(float) * M)); D.kappa = static_cast<float*>(p);
   CP_TRY(g2_alloc(g, &p, sizeof(float2) * (Ny / 2))); D.tw = static_cast<float2*>(p);
@@ -1503,6 +1504,9 @@ int g2_init(cp_gap2d* g, int mode, double tol) {
   CP_CUDA(cpk::tables2_launch(g->dD, Ny, (D.dx / D.dy) * (D.dx / D.dy), c->stream));
   int per_sm = 0;
   CP_CUDA(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, c->device));
+  CP_TRY(g2_alloc(g, &p, sizeof(int) * 2 * g->sms * T));
+  D.bhist = static_cast<int*>(p);
+  CP_CUDA(cudaMemcpyAsync(&g->dD->bhist, &D.bhist, sizeof(int*), cudaMemcpyHostToDevice, c->stream));
   CP_CUDA(cpk::push2_occupancy(&per_sm));
   if (per_sm < 1) return CP_ERR_ARG;
   g->grid = per_sm * g->sms;

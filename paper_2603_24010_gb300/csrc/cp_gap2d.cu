@@ -465,6 +465,15 @@ __device__ __forceinline__ int tile_of(const Dev2D& D, float x, float y) {
   return tx * D.nty + ty;
 }
 
+// Counting sort in three passes, each block owning one contiguous range of
+// slots: per-block tile histograms, then (one block) the tile segments and
+// every block's base in each tile, then the scatter with shared-memory
+// cursors -- no global atomics on the per-tile cursors.
+__device__ __forceinline__ void block_range(long long n, long long* b0, long long* b1) {
+  *b0 = n * blockIdx.x / gridDim.x;
+  *b1 = n * (blockIdx.x + 1) / gridDim.x;
+}
+
 __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
   extern __shared__ int hist[];
   const Dev2D& D = *Dp;
@@ -472,36 +481,35 @@ __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
   __syncthreads();
   const float* xs = reinterpret_cast<const float*>(S->xi[s]);
   const float* ys = reinterpret_cast<const float*>(D.y[s]);
-  const long long n = S->n_proc[s];
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
-       k += static_cast<long long>(gridDim.x) * blockDim.x) {
+  long long b0, b1;
+  block_range(S->n_proc[s], &b0, &b1);
+  for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
     const float x = xs[k];
     if (x > 0.0f && x < D.Nxf) atomicAdd(&hist[tile_of(D, x, ys[k])], 1);
   }
   __syncthreads();
-  int* cnt = D.tile_cnt + s * D.T;
-  for (int t = threadIdx.x; t < D.T; t += blockDim.x)
-    if (hist[t]) atomicAdd(&cnt[t], hist[t]);
+  int* bh = D.bhist + static_cast<long long>(blockIdx.x) * D.T;
+  for (int t = threadIdx.x; t < D.T; t += blockDim.x) bh[t] = hist[t];
 }
 
-// one block: tile segment starts (padded to 4), work-item prefix, cursors,
-// dead padding in the destination
-__global__ void k2_scan(DevState* S, Dev2D* Dp, int s) {
+// one block: tile totals and per-block offsets, tile segment starts (padded
+// to 4), work-item prefix, dead padding in the destination, block bases
+__global__ void k2_scan(DevState* S, Dev2D* Dp, int s, int G) {
   Dev2D& D = *Dp;
   __shared__ int wsum[32], wsum2[32];
   const int T = D.T;
   int* cnt = D.tile_cnt + s * T;
   int* ts = D.tile_start + s * (T + 1);
   int* wo = D.wi_off + s * (T + 1);
-  int* cur = D.tile_cur + s * T;
+  (void)G;
   const int per = (T + blockDim.x - 1) / blockDim.x;
   const int t0 = min(static_cast<int>(threadIdx.x) * per, T), t1 = min(t0 + per, T);
-  int a = 0, b = 0;
+  int a = 0, bq = 0;
   for (int t = t0; t < t1; ++t) {
     a += (cnt[t] + 3) & ~3;
-    b += (cnt[t] + kChunk2 - 1) / kChunk2;
+    bq += (cnt[t] + kChunk2 - 1) / kChunk2;
   }
-  int ia = a, ib = b;
+  int ia = a, ib = bq;
   for (int o = 1; o < 32; o <<= 1) {
     const int ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
     if (static_cast<int>(lane_id()) >= o) {
@@ -520,14 +528,13 @@ __global__ void k2_scan(DevState* S, Dev2D* Dp, int s) {
     ba += wsum[q];
     bb += wsum2[q];
   }
-  int ra = ba + ia - a, rb = bb + ib - b;
+  int ra = ba + ia - a, rb = bb + ib - bq;
   float* xd = reinterpret_cast<float*>(S->xi_alt[s]);
   float* ud = reinterpret_cast<float*>(S->u_alt[s]);
   const long long cap = D.cap[s];
   for (int t = t0; t < t1; ++t) {
     ts[t] = ra;
     wo[t] = rb;
-    cur[t] = ra;
     const int c = cnt[t], c4 = (c + 3) & ~3;
     for (int k = c; k < c4; ++k) {  // dead padding slots
       if (ra + k < cap) {
@@ -544,10 +551,52 @@ __global__ void k2_scan(DevState* S, Dev2D* Dp, int s) {
   }
 }
 
+// one block per tile: exclusive scan of the per-block counts over the blocks
+// (each block's offset within the tile) and the tile's total
+__global__ void k2_tilescan(Dev2D* Dp, int s, int G) {
+  Dev2D& D = *Dp;
+  __shared__ int wsum[32];
+  const int t = blockIdx.x, T = D.T;
+  const int per = (G + blockDim.x - 1) / blockDim.x;
+  const int b0 = min(static_cast<int>(threadIdx.x) * per, G), b1 = min(b0 + per, G);
+  int loc = 0;
+  for (int b = b0; b < b1; ++b) loc += D.bhist[static_cast<long long>(b) * T + t];
+  int incl = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (static_cast<int>(lane_id()) >= o) incl += y;
+  }
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 31) wsum[w] = incl;
+  __syncthreads();
+  int base = 0;
+  for (int q = 0; q < w; ++q) base += wsum[q];
+  int run = base + incl - loc;
+  for (int b = b0; b < b1; ++b) {
+    int* p = D.bhist + static_cast<long long>(b) * T + t;
+    const int c = *p;
+    *p = run;
+    run += c;
+  }
+  if (threadIdx.x == blockDim.x - 1) D.tile_cnt[s * T + t] = base + incl;
+}
+
+// block bases: tile start + the block's offset within the tile
+__global__ void k2_bases(Dev2D* Dp, int s, int G) {
+  Dev2D& D = *Dp;
+  const long long n = static_cast<long long>(G) * D.T;
+  const int* ts = D.tile_start + s * (D.T + 1);
+  for (long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; q < n;
+       q += static_cast<long long>(gridDim.x) * blockDim.x)
+    D.bhist[q] += ts[q % D.T];
+}
+
 __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
-  extern __shared__ int sm[];
+  extern __shared__ int cur[];
   const Dev2D& D = *Dp;
-  int* loc = sm;           // per-tile count in this block, then the block's base
+  const int* bh = D.bhist + static_cast<long long>(blockIdx.x) * D.T;
+  for (int t = threadIdx.x; t < D.T; t += blockDim.x) cur[t] = bh[t];
+  __syncthreads();
   const float* xs = reinterpret_cast<const float*>(S->xi[s]);
   const float* us = reinterpret_cast<const float*>(S->u[s]);
   const float* ys = reinterpret_cast<const float*>(D.y[s]);
@@ -558,42 +607,19 @@ __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
   float* wd = reinterpret_cast<float*>(D.w_alt[s]);
   const uint32_t* is = S->id;
   uint32_t* id_d = S->id_alt;
-  const long long n = S->n_proc[s];
-  const long long chunk = static_cast<long long>(blockDim.x) * 8;
-  for (long long c0 = static_cast<long long>(blockIdx.x) * chunk; c0 < n;
-       c0 += static_cast<long long>(gridDim.x) * chunk) {
-    for (int t = threadIdx.x; t < D.T; t += blockDim.x) loc[t] = 0;
-    __syncthreads();
-    int tl[8], rank[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const long long k = c0 + threadIdx.x + static_cast<long long>(q) * blockDim.x;
-      tl[q] = -1;
-      if (k < n) {
-        const float x = xs[k];
-        if (x > 0.0f && x < D.Nxf) {
-          tl[q] = tile_of(D, x, ys[k]);
-          rank[q] = atomicAdd(&loc[tl[q]], 1);
-        }
-      }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < D.T; t += blockDim.x)
-      if (loc[t]) loc[t] = atomicAdd(&D.tile_cur[s * D.T + t], loc[t]);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (tl[q] < 0) continue;
-      const long long k = c0 + threadIdx.x + static_cast<long long>(q) * blockDim.x;
-      const long long o = static_cast<long long>(loc[tl[q]]) + rank[q];
-      if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
-      xd[o] = xs[k];
-      ud[o] = us[k];
-      yd[o] = ys[k];
-      wd[o] = ws[k];
-      if (s == CP_IONS) id_d[o] = is[k];
-    }
-    __syncthreads();
+  long long b0, b1;
+  block_range(S->n_proc[s], &b0, &b1);
+  for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+    const float x = xs[k];
+    if (!(x > 0.0f && x < D.Nxf)) continue;
+    const float y = ys[k];
+    const long long o = atomicAdd(&cur[tile_of(D, x, y)], 1);
+    if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
+    xd[o] = x;
+    ud[o] = us[k];
+    yd[o] = y;
+    wd[o] = ws[k];
+    if (s == CP_IONS) id_d[o] = is[k];
   }
 }
 
@@ -618,7 +644,6 @@ __global__ void k2_swap(DevState* S, Dev2D* Dp, int s) {
   D.n_sorted[s] = n;
   S->n_alloc[s] = n;
   S->n_proc[s] = n;
-  for (int k = 0; k < D.T; ++k) D.tile_cnt[s * D.T + k] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -690,33 +715,61 @@ __global__ void k2_fwd(Dev2D* Dp, long long* G1) {
   for (int k = threadIdx.x; k <= Ny / 2; k += blockDim.x) R[k] = buf[k];
 }
 
-// one thread per mode k = 1..Ny/2: Thomas over i = 1..Nx-1, phi = 0 at both ends:
-// Phi_{i-1} - (2 + kappa_k) Phi_i + Phi_{i+1} = -dx^2 R_i / eps0
-__global__ void k2_modes(Dev2D* Dp, float c_rhs) {
+// One thread per mode k = 1..Ny/2: Thomas over i = 1..Nx-1 with phi = 0 at
+// both ends for  Phi_{i-1} - (2 + kappa_k) Phi_i + Phi_{i+1} = -dx^2 R_i / eps0.
+// The elimination factors depend on (i, k) only and are tabulated once
+// (k2_tables); a step runs the two substitutions, 16 rows of loads ahead.
+constexpr int kU2 = 16;
+__global__ void __launch_bounds__(64) k2_modes(Dev2D* Dp, float c_rhs) {
   const Dev2D& D = *Dp;
   const int k = 1 + blockIdx.x * blockDim.x + threadIdx.x;
   const int M = D.Ny / 2 + 1;
   if (k >= M) return;
-  const float b = -(2.0f + D.kappa[k]);
-  float cprev = 0.0f;
-  float2 dprev = make_float2(0.0f, 0.0f);
-  for (int i = 1; i < D.Nx; ++i) {
-    const float den = b - cprev;
-    const float inv = 1.0f / den;
-    const float c = (i + 1 < D.Nx) ? inv : 0.0f;
-    const float2 r = D.R[static_cast<long long>(i) * M + k];
-    const float2 d = make_float2((c_rhs * r.x - dprev.x) * inv, (c_rhs * r.y - dprev.y) * inv);
-    D.cp[static_cast<long long>(i) * M + k] = c;
-    D.R[static_cast<long long>(i) * M + k] = d;
-    cprev = c;
-    dprev = d;
+  float2* __restrict__ R = D.R;
+  const float* __restrict__ inv = D.tinv;
+  const float* __restrict__ cp = D.cp;
+  const int n = D.Nx - 1;  // rows 1..n
+  float2 d = make_float2(0.0f, 0.0f);
+  for (int i0 = 1; i0 <= n; i0 += kU2) {
+    float2 r[kU2];
+    float iv[kU2];
+#pragma unroll
+    for (int q = 0; q < kU2; ++q) {
+      const int i = i0 + q;
+      if (i <= n) {
+        r[q] = R[static_cast<long long>(i) * M + k];
+        iv[q] = inv[static_cast<long long>(i) * M + k];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kU2; ++q) {
+      const int i = i0 + q;
+      if (i <= n) {
+        d = make_float2((c_rhs * r[q].x - d.x) * iv[q], (c_rhs * r[q].y - d.y) * iv[q]);
+        R[static_cast<long long>(i) * M + k] = d;
+      }
+    }
   }
   float2 x = make_float2(0.0f, 0.0f);
-  for (int i = D.Nx - 1; i >= 1; --i) {
-    const float2 d = D.R[static_cast<long long>(i) * M + k];
-    const float c = D.cp[static_cast<long long>(i) * M + k];
-    x = make_float2(d.x - c * x.x, d.y - c * x.y);
-    D.R[static_cast<long long>(i) * M + k] = x;
+  for (int i0 = n; i0 >= 1; i0 -= kU2) {
+    float2 dd[kU2];
+    float cc[kU2];
+#pragma unroll
+    for (int q = 0; q < kU2; ++q) {
+      const int i = i0 - q;
+      if (i >= 1) {
+        dd[q] = R[static_cast<long long>(i) * M + k];
+        cc[q] = cp[static_cast<long long>(i) * M + k];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kU2; ++q) {
+      const int i = i0 - q;
+      if (i >= 1) {
+        x = make_float2(dd[q].x - cc[q] * x.x, dd[q].y - cc[q] * x.y);
+        R[static_cast<long long>(i) * M + k] = x;
+      }
+    }
   }
 }
 
@@ -763,12 +816,23 @@ __global__ void k2_fields(Dev2D* Dp, const double* __restrict__ E64) {
 
 __global__ void k2_tables(Dev2D* Dp, double r2) {
   Dev2D& D = *Dp;
-  const int Ny = D.Ny;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= Ny / 2; k += gridDim.x * blockDim.x) {
+  const int Ny = D.Ny, M = Ny / 2 + 1;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
     double sn, cs;
     sincospi(2.0 * k / Ny, &sn, &cs);
-    D.kappa[k] = static_cast<float>(r2 * (2.0 - 2.0 * cs));
+    const double kap = r2 * (2.0 - 2.0 * cs);
+    D.kappa[k] = static_cast<float>(kap);
     if (k < Ny / 2) D.tw[k] = make_float2(static_cast<float>(cs), static_cast<float>(-sn));
+    // Thomas elimination of mode k: inv_i = 1/(b - c'_{i-1}), c'_i = inv_i (last row 0)
+    const double bk = -(2.0 + kap);
+    double cprev = 0.0;
+    for (int i = 1; i < D.Nx; ++i) {
+      const double iv = 1.0 / (bk - cprev);
+      const double c = (i + 1 < D.Nx) ? iv : 0.0;
+      D.tinv[static_cast<long long>(i) * M + k] = static_cast<float>(iv);
+      D.cp[static_cast<long long>(i) * M + k] = static_cast<float>(c);
+      cprev = c;
+    }
   }
 }
 
@@ -802,9 +866,12 @@ cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* a
 cudaError_t sort2_launch(DevState* S, void* D, int T, int s, int sms, cudaStream_t st) {
   Dev2D* Dp = static_cast<Dev2D*>(D);
   const size_t hs = sizeof(int) * T;
-  k2_hist<<<2 * sms, 512, hs, st>>>(S, Dp, s);
-  k2_scan<<<1, 1024, 0, st>>>(S, Dp, s);
-  k2_scatter<<<2 * sms, 512, hs, st>>>(S, Dp, s);
+  const int G = 2 * sms;  // must match the blocks the per-block histograms were sized for
+  k2_hist<<<G, 512, hs, st>>>(S, Dp, s);
+  k2_tilescan<<<T, 128, 0, st>>>(Dp, s, G);
+  k2_scan<<<1, 1024, 0, st>>>(S, Dp, s, G);
+  k2_bases<<<std::min(4096, (G * T + 255) / 256), 256, 0, st>>>(Dp, s, G);
+  k2_scatter<<<G, 512, hs, st>>>(S, Dp, s);
   k2_swap<<<1, 1, 0, st>>>(S, Dp, s);
   return cudaGetLastError();
 }
@@ -828,7 +895,7 @@ cudaError_t solve2_modes_launch(void* D, int Nx, int Ny, float c_rhs, const doub
                                 cudaStream_t st) {
   Dev2D* Dp = static_cast<Dev2D*>(D);
   const int M = Ny / 2;
-  k2_modes<<<(M + 31) / 32, 32, 0, st>>>(Dp, c_rhs);
+  k2_modes<<<(M + 63) / 64, 64, 0, st>>>(Dp, c_rhs);
   if (Nx > 1) k2_inv<<<Nx - 1, 256, sizeof(float2) * Ny, st>>>(Dp);
   const long long n = static_cast<long long>(Nx + 1) * Ny;
   const int grid = static_cast<int>(std::min<long long>((n + 255) / 256, 4096));

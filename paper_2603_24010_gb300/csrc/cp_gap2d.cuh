@@ -39,7 +39,9 @@ struct Dev2D {
   long long* G2;    // [Nx+1][Ny] charge being deposited
   long long* G2last;
   float2* R;        // [Nx+1][Ny/2+1] transverse spectra
-  float* cp;        // [Nx+1][Ny/2+1] Thomas scratch
+  float* cp;        // [Nx+1][Ny/2+1] Thomas factors c'_i of each mode
+  float* tinv;      // [Nx+1][Ny/2+1] Thomas factors 1/(b - c'_{i-1}) of each mode
+  int* bhist;       // [sort blocks][T] per-block tile counts, then bases
   float* phit;      // [Nx+1][Ny] potential of the k != 0 modes
   float* kappa;     // [Ny/2+1] (dx/dy)^2 (2 - 2 cos 2 pi k/Ny)
   float2* tw;       // [Ny/2] exp(-2 pi i k/Ny)
