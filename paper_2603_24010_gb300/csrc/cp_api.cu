@@ -83,6 +83,7 @@ struct cp_ctx {
   int64_t hist_rows = 0;
   double* vs = nullptr;
   int grid = 0;
+  int compact_grid = 0;   // removal kernel
   size_t smem = 0;        // push kernel
   size_t solve_smem = 0;  // solve kernel
   int solve_ctas = 8;     // CTAs in the solve's cluster
@@ -245,6 +246,7 @@ int initialize(cp_ctx* c, int mode, double tol) {
   CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   if (per_sm < 1) return CP_ERR_ARG;
   c->grid = per_sm * sms;
+  c->compact_grid = 2 * sms;
   c->hp.abs_cap = 4096;
   CP_TRY(alloc(reinterpret_cast<void**>(&c->abs),
                sizeof(cpk::AbsRec) * (c->ens_member ? size_t(1)
@@ -308,7 +310,7 @@ int build_graph(cp_ctx* c, int mode, double tol) {
     e = cpk::push_launch(c->precision, B, c->grid, c->smem, c->cap_stream, 1);
     if (e == cudaSuccess) e = cpk::solve_launch(c->precision, B, c->solve_ctas, c->solve_smem, c->cap_stream, 1, mode, tol);
   }
-  if (e == cudaSuccess) e = cpk::compact_launch(c->precision, B, c->grid, c->cap_stream);
+  if (e == cudaSuccess) e = cpk::compact_launch(c->precision, B, c->compact_grid, c->cap_stream);
   const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -336,7 +338,7 @@ int timed_launch(cp_ctx* c, int which, int mode, double tol, std::vector<std::pa
   else if (which == 1)
     CP_CUDA(cpk::solve_launch(c->precision, B, c->solve_ctas, c->solve_smem, c->stream, 1, mode, tol));
   else
-    CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
+    CP_CUDA(cpk::compact_launch(c->precision, B, c->compact_grid, c->stream));
   CP_CUDA(cudaEventRecord(c->ev_pool[k + 1], c->stream));
   rec->push_back({which, k});
   return CP_OK;
@@ -395,7 +397,7 @@ int do_steps(cp_ctx* c, int mode, int32_t n_steps, double tol) {
     c->launches += 2;
     --left;
     if (++c->since_compact == c->compact_every) {
-      CP_CUDA(cpk::compact_launch(c->precision, B, c->grid, c->stream));
+      CP_CUDA(cpk::compact_launch(c->precision, B, c->compact_grid, c->stream));
       c->launches += 1;
       c->since_compact = 0;
     }

@@ -80,6 +80,20 @@ __device__ __forceinline__ float bilin(float f00, float f10, float f01, float f1
   return (1.0f - b) * ((1.0f - a) * f00 + a * f10) + b * ((1.0f - a) * f01 + a * f11);
 }
 
+// window index of a 2x2 stencil's origin node (gx, gy) when the whole
+// stencil lies in the window (origin at most kW2-2 from the window's edge);
+// -1 otherwise
+__device__ __forceinline__ int win_rel(int gx, int gy, int ox, int oy, int Ny) {
+  const int lx = gx - ox;
+  int ly = gy - oy;
+  if (ly < 0) ly += Ny;
+  else if (ly >= Ny) ly -= Ny;
+  if (static_cast<unsigned>(lx) > static_cast<unsigned>(kW2 - 2) ||
+      static_cast<unsigned>(ly) > static_cast<unsigned>(kW2 - 2))
+    return -1;
+  return lx * kW2 + ly;
+}
+
 // window coordinates of a global node (x index gx, y index gy); -1 if outside
 __device__ __forceinline__ int win_index(int gx, int gy, int ox, int oy, int Ny) {
   const int lx = gx - ox;
@@ -197,7 +211,7 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
       for (int q = threadIdx.x; win && q < kW2 * kW2; q += kThreads2) {
         const int lx = q / kW2, ly = q % kW2;
         const int gx = ox + lx;
-        const int gy = modp(oy + ly, Ny);
+        const int gy = wrapi(oy + ly, Ny);  // one wrap: Ny >= the window edge
         Exw[q] = (gx >= 0 && gx < D.Nx) ? D.Ex[static_cast<long long>(gx) * Ny + gy] : 0.0f;
         Eyw[q] = (gx >= 0 && gx <= D.Nx) ? D.Ey[static_cast<long long>(gx) * Ny + gy] : 0.0f;
         Dw[q] = 0u;
@@ -229,15 +243,14 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
           if (!(x > 0.0f && x < D.Nxf)) continue;  // dead slot
           const Stencil2 st = stencil2(D, x, yv[q]);
           float ex, ey;
-          const int e00 = win ? win_index(st.i, st.j, ox, oy, Ny) : -1;
-          const int e11 = win ? win_index(st.i1, st.j1, ox, oy, Ny) : -1;
-          const int f00 = win ? win_index(st.a, st.jj, ox, oy, Ny) : -1;
-          const int f11 = win ? win_index(st.a1, st.jj1, ox, oy, Ny) : -1;
-          if (e00 >= 0 && e11 >= 0 && f00 >= 0 && f11 >= 0) {
-            const int e10 = win_index(st.i1, st.j, ox, oy, Ny), e01 = win_index(st.i, st.j1, ox, oy, Ny);
-            const int f10 = win_index(st.a1, st.jj, ox, oy, Ny), f01 = win_index(st.a, st.jj1, ox, oy, Ny);
-            ex = bilin(Exw[e00], Exw[e10], Exw[e01], Exw[e11], st.t, st.v);
-            ey = bilin(Eyw[f00], Eyw[f10], Eyw[f01], Eyw[f11], st.fx, st.vy);
+          // window origins of the two 2x2 stencils (the window is contiguous in
+          // y, so the corners sit at +1 row / +1 column of their origin)
+          const int le = win_rel(st.i, st.j, ox, oy, Ny), lf = win_rel(st.a, st.jj, ox, oy, Ny);
+          if (win && le >= 0 && lf >= 0) {
+            const int e00 = le, e10 = le + (st.i1 - st.i) * kW2;
+            const int f00 = lf, f10 = lf + kW2;
+            ex = bilin(Exw[e00], Exw[e10], Exw[e00 + 1], Exw[e10 + 1], st.t, st.v);
+            ey = bilin(Eyw[f00], Eyw[f10], Eyw[f00 + 1], Eyw[f10 + 1], st.fx, st.vy);
           } else {
             const float* Ex = D.Ex;
             const float* Ey = D.Ey;
@@ -289,10 +302,9 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
           wv[q] = wn;
           int i, j, j1, w00, w10, w01, w11;
           deposit_weights(xn, yn, Ny, &i, &j, &j1, &w00, &w10, &w01, &w11);
-          const int d00 = win ? win_index(i, j, ox, oy, Ny) : -1;
-          const int d11 = win ? win_index(i + 1, j1, ox, oy, Ny) : -1;
-          if (d00 >= 0 && d11 >= 0) {
-            const int d10 = win_index(i + 1, j, ox, oy, Ny), d01 = win_index(i, j1, ox, oy, Ny);
+          const int d00 = win ? win_rel(i, j, ox, oy, Ny) : -1;
+          if (d00 >= 0) {
+            const int d10 = d00 + kW2, d01 = d00 + 1, d11 = d10 + 1;
             if (w00) atomicAdd(&Dw[d00], static_cast<unsigned int>(w00));
             if (w10) atomicAdd(&Dw[d10], static_cast<unsigned int>(w10));
             if (w01) atomicAdd(&Dw[d01], static_cast<unsigned int>(w01));
@@ -313,7 +325,7 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         const unsigned int v = Dw[q];
         if (v == 0u) continue;
         const int gx = ox + q / kW2;
-        const int gy = modp(oy + q % kW2, Ny);
+        const int gy = wrapi(oy + q % kW2, Ny);
         const long long dbl = (gx == 0 || gx == D.Nx) ? 2 : 1;
         atomic_add_i64(&D.G2[static_cast<long long>(gx) * Ny + gy], sign * dbl * static_cast<long long>(v));
       }
@@ -483,9 +495,17 @@ __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
   const float* ys = reinterpret_cast<const float*>(D.y[s]);
   long long b0, b1;
   block_range(S->n_proc[s], &b0, &b1);
-  for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
-    const float x = xs[k];
-    if (x > 0.0f && x < D.Nxf) atomicAdd(&hist[tile_of(D, x, ys[k])], 1);
+  // warp-uniform trips; lanes of one tile (sorted data: most of a warp)
+  // are counted by one shared-memory atomic
+  for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += blockDim.x) {
+    const long long k = k0 + lane_id();
+    int t = -1;
+    if (k < b1) {
+      const float x = xs[k];
+      if (x > 0.0f && x < D.Nxf) t = tile_of(D, x, ys[k]);
+    }
+    const unsigned m = __match_any_sync(0xffffffffu, t);
+    if (t >= 0 && static_cast<int>(lane_id()) == __ffs(m) - 1) atomicAdd(&hist[t], __popc(m));
   }
   __syncthreads();
   int* bh = D.bhist + static_cast<long long>(blockIdx.x) * D.T;
@@ -609,11 +629,24 @@ __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
   uint32_t* id_d = S->id_alt;
   long long b0, b1;
   block_range(S->n_proc[s], &b0, &b1);
-  for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
-    const float x = xs[k];
-    if (!(x > 0.0f && x < D.Nxf)) continue;
-    const float y = ys[k];
-    const long long o = atomicAdd(&cur[tile_of(D, x, y)], 1);
+  for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += blockDim.x) {
+    const long long k = k0 + lane_id();
+    int t = -1;
+    float x = 0.0f, y = 0.0f;
+    if (k < b1) {
+      x = xs[k];
+      if (x > 0.0f && x < D.Nxf) {
+        y = ys[k];
+        t = tile_of(D, x, y);
+      }
+    }
+    const unsigned m = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (t >= 0 && static_cast<int>(lane_id()) == leader) base = atomicAdd(&cur[t], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (t < 0) continue;
+    const long long o = static_cast<long long>(base) + __popc(m & ((1u << lane_id()) - 1u));
     if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
     xd[o] = x;
     ud[o] = us[k];
