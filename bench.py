@@ -57,7 +57,7 @@ def workload(name, seed, pairs=None):
 
 PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_gap_1d_fp32_large.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2603_24010_gb300", "csrc", f)
-                  for f in ("cp_push_tma.cu", "cp_push.cu", "cp_common.cuh", "cp_device.cuh")]
+                  for f in ("cp_push_async.cu", "cp_push.cu", "cp_common.cuh", "cp_device.cuh")]
 
 
 def kernel_source_hash():

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["cp_push.cu", "cp_push_tma.cu", "cp_solve.cu", "cp_batch.cu", "cp_gap2d.cu", "cp_mlp.cu", "cp_api.cu",
+SOURCES = ["cp_push.cu", "cp_push_async.cu", "cp_solve.cu", "cp_batch.cu", "cp_gap2d.cu", "cp_mlp.cu", "cp_api.cu",
            "cp_noalloc.cu"]
 LIB = os.path.join(HERE, "libcp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

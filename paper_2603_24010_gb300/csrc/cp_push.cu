@@ -421,27 +421,27 @@ __global__ void k_fill(real* p, int64_t n, real v) {
 // ---------------------------------------------------------------------------
 // Host-side launchers (internal C++ interface used by cp_api.cu)
 // ---------------------------------------------------------------------------
-// FP32 particles take the bulk-copy pipelined push of cp_push_tma.cu.
-size_t push_tma_smem_bytes(int N);
-cudaError_t push_tma_configure(size_t smem);
-cudaError_t push_tma_occupancy(size_t smem, int* blocks_per_sm);
-cudaError_t push_tma_launch(const Bufs& B, int grid, size_t smem, cudaStream_t st, int do_push);
+// FP32 particles take the push of cp_push_async.cu.
+size_t push_async_smem_bytes(int N);
+cudaError_t push_async_configure(size_t smem);
+cudaError_t push_async_occupancy(size_t smem, int* blocks_per_sm);
+cudaError_t push_async_launch(const Bufs& B, int grid, size_t smem, cudaStream_t st, int do_push);
 
 cudaError_t push_configure(int precision, size_t push_smem) {
-  if (precision == CP_FP32) return push_tma_configure(push_smem);
+  if (precision == CP_FP32) return push_async_configure(push_smem);
   return cudaFuncSetAttribute(k_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(push_smem));
 }
 
 size_t push_smem_bytes(int N, int precision) {
-  if (precision == CP_FP32) return push_tma_smem_bytes(N);
+  if (precision == CP_FP32) return push_async_smem_bytes(N);
   const size_t es = (precision == CP_FP32) ? sizeof(float) : sizeof(double);
   return align16(sizeof(long long) * (N + 1)) + align16(sizeof(unsigned int) * 2 * N) +
          2 * es * (N + 1);
 }
 
 cudaError_t push_occupancy(int precision, size_t smem, int* blocks_per_sm) {
-  if (precision == CP_FP32) return push_tma_occupancy(smem, blocks_per_sm);
+  if (precision == CP_FP32) return push_async_occupancy(smem, blocks_per_sm);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<double>, kThreads, smem);
 }
 
@@ -460,7 +460,7 @@ cudaError_t push_launch(int precision, const Bufs& B, int grid, size_t smem, cud
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (precision == CP_FP32) return push_tma_launch(B, grid, smem, st, do_push);
+  if (precision == CP_FP32) return push_async_launch(B, grid, smem, st, do_push);
   return cudaLaunchKernelEx(&cfg, k_push<double>, B, do_push);
 }
 

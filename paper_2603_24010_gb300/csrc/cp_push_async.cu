@@ -1,0 +1,386 @@
+// cp_push_async.cu -- the FP32 particle push with per-thread asynchronous
+// copies.
+//
+// Same step as k_push (gather, kick, drift, absorption, SEE, beam, fixed-
+// point deposit; Sec. 2.2.2, 2.3, 2.4.1, App. C, App. E.2), with the HBM
+// stream kept deeper in flight: every thread owns a ring of three 32-byte
+// slots in shared memory (x and u of its four particles of a tile) filled by
+// cp.async copies, so two tiles are always on their way while the third is
+// processed, without holding registers for them and without block-wide
+// synchronisation (each thread waits only for its own copy groups).  To make
+// room for the ring at two CTAs per SM, the field table keeps only the N
+// half-grid values (the slope is recomputed from neighbours exactly as the
+// solve forms it) and the deposit uses one 32-bit sum per node.
+#include "cp_common.cuh"
+
+namespace cpk {
+
+constexpr int kAStages = 3;  // slots per thread: two tiles in flight, one processed
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte global -> shared copy, cached in L2 only
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// fold the node sums into the int64 grid (end nodes doubled) and clear them
+__device__ __forceinline__ void fold_nodes(unsigned int* nd, long long* Gs, int N, long long sign) {
+  for (int k = threadIdx.x; k <= N; k += kThreads) {
+    long long a = nd[k];
+    if (a) {
+      nd[k] = 0u;
+      if (k == 0 || k == N) a <<= 1;
+      Gs[k] += sign * a;
+    }
+  }
+}
+
+// CIC deposit of one particle into the node sums: node i gets 2^16 - W1, node i+1 W1
+__device__ __forceinline__ void deposit_nodes(unsigned int* nd, float x) {
+  const float fl = floorf(x);
+  const int i = static_cast<int>(fl);
+  const unsigned int w1 = frac_to_fix(x - fl);
+  atomicAdd(&nd[i], 65536u - w1);
+  atomicAdd(&nd[i + 1], w1);
+}
+
+// gather from the field table E[0..N-1] (E_{j+1/2}); the pair (E_j, slope)
+// of the pair table is formed here with the same FP32 subtraction
+__device__ __forceinline__ float gather_tab(const float* Et, int N, float x) {
+  const float s = x - 0.5f;
+  const float jf = floorf(s);
+  const int j = static_cast<int>(jf);
+  const float t = s - jf;
+  float e0, d;
+  if (j < 0) {
+    e0 = Et[0];
+    d = 0.0f;
+  } else if (j >= N - 1) {
+    e0 = Et[N - 1];
+    d = 0.0f;
+  } else {
+    e0 = Et[j];
+    d = Et[j + 1] - e0;
+  }
+  return fmaf(t, d, e0);
+}
+
+constexpr size_t kRingBytes = static_cast<size_t>(kAStages) * kThreads * 32;
+
+size_t push_async_smem_bytes(int N) {
+  return kRingBytes + align16(sizeof(long long) * (N + 1)) + align16(sizeof(unsigned int) * (N + 1)) +
+         align16(sizeof(float) * N);
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int do_push) {
+  const DevParams* __restrict__ P = B.P;
+  DevState* S = B.S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_abs_n;
+  __shared__ int s_flag[2];  // [0] stopped, [1] overflow
+  __shared__ unsigned long long s_cnt[2][kSpecies];
+  __shared__ unsigned long long s_emit[2];
+  __shared__ long long s_conv, s_energy;
+  __shared__ unsigned int s_cfl;
+
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  if (threadIdx.x == 0) {
+    s_flag[0] = (ldcg(&S->status) != 0);
+    s_flag[1] = 0;
+    s_abs_n = 0;
+    s_conv = 0;
+    s_energy = 0;
+    s_cfl = 0u;
+    s_emit[0] = s_emit[1] = 0ULL;
+  }
+  if (threadIdx.x < 2 * kSpecies) s_cnt[threadIdx.x / kSpecies][threadIdx.x % kSpecies] = 0ULL;
+  __syncthreads();
+  if (s_flag[0]) return;
+
+  const int N = P->N;
+  const int64_t step = S->level;
+  float4* ring = reinterpret_cast<float4*>(smem);  // [stage][x | u][thread]
+  long long* Gs = reinterpret_cast<long long*>(smem + kRingBytes);
+  unsigned int* nd = reinterpret_cast<unsigned int*>(smem + kRingBytes + align16(sizeof(long long) * (N + 1)));
+  float* Et = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(nd) + align16(sizeof(unsigned int) * (N + 1)));
+  const float2* Epair = reinterpret_cast<const float2*>(B.Epair);
+  for (int k = threadIdx.x; k <= N; k += kThreads) {
+    Gs[k] = 0;
+    nd[k] = 0u;
+    if (k < N) Et[k] = Epair[k + 1].x;
+  }
+  __syncthreads();
+
+  const bool half = (S->pushed == 0);
+  const float Nr = static_cast<float>(N);
+  const int cap = P->abs_cap;
+  AbsRec* my_abs = B.abs + static_cast<size_t>(blockIdx.x) * cap;
+  unsigned int cfl = 0u;
+  float4* my_slot = ring + threadIdx.x;  // x at + stage * 2 kThreads, u kThreads further
+
+  for (int s = 0; s < kSpecies; ++s) {
+    float* __restrict__ xs = reinterpret_cast<float*>(S->xi[s]);
+    float* __restrict__ us = reinterpret_cast<float*>(S->u[s]);
+    const int64_t n = S->n_proc[s];  // multiple of 4
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    const int64_t mine = (ntiles > blockIdx.x) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long sign = (s == CP_IONS) ? 1LL : -1LL;
+    const float kap = P->kap_f[half ? 0 : 1][s];
+    const uint32_t* ids = S->id;
+    unsigned int a0 = 0u, a1 = 0u;
+    int since = 0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kTile;
+    const int64_t base0 = static_cast<int64_t>(blockIdx.x) * kTile + static_cast<int64_t>(threadIdx.x) * kPerThread;
+    auto issue = [&](int64_t j) {  // this thread's four particles of its j-th tile
+      const int64_t b = base0 + j * stride;
+      float4* slot = my_slot + static_cast<int>(j % kAStages) * kThreads * 2;
+      if (j < mine && b < n) {
+        cp_async16(slot, xs + b);
+        if (do_push) cp_async16(slot + kThreads, us + b);
+      }
+      cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    for (int64_t j = 0; j < mine; ++j) {
+      issue(j + 2);
+      cp_async_wait<2>();  // this thread's copies of tile j have landed
+      const int64_t base = base0 + j * stride;
+      if (base < n) {
+        const float4* slot = my_slot + static_cast<int>(j % kAStages) * kThreads * 2;
+        const float4 xa = slot[0];
+        float xv[4] = {xa.x, xa.y, xa.z, xa.w};
+        if (do_push) {
+          const float4 ua = slot[kThreads];
+          float uv[4] = {ua.x, ua.y, ua.z, ua.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (xv[q] > 0.0f && xv[q] < Nr) {  // live (dead slots hold -1)
+              const float E = gather_tab(Et, N, xv[q]);
+              const float un = fmaf(kap, E, uv[q]);
+              const float xn = xv[q] + un;
+              cfl = max(cfl, __float_as_uint(fabsf(un)));
+              if (!(xn > 0.0f && xn < Nr)) {  // absorbed (a non-finite value counts at x = d)
+                const int el = (xn <= 0.0f) ? 0 : 1;
+                if (el) ++a1; else ++a0;
+                if (s == CP_IONS) {
+                  const int slot_i = atomicAdd(&s_abs_n, 1);
+                  if (slot_i < cap) {
+                    AbsRec r;
+                    r.id = ids[base + q];
+                    r.electrode = static_cast<uint32_t>(el);
+                    r.u = static_cast<double>(un);
+                    my_abs[slot_i] = r;
+                  }
+                }
+                xv[q] = -1.0f;
+                uv[q] = 0.0f;
+              } else {
+                deposit_nodes(nd, xn);
+                xv[q] = xn;
+                uv[q] = un;
+              }
+            }
+          }
+          store4(xs + base, xv);
+          store4(us + base, uv);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (xv[q] > 0.0f && xv[q] < Nr) deposit_nodes(nd, xv[q]);
+        }
+      }
+      if (++since == kFlushTiles) {  // bounds every 32-bit node sum below 2^32
+        __syncthreads();
+        fold_nodes(nd, Gs, N, sign);
+        __syncthreads();
+        since = 0;
+      }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    fold_nodes(nd, Gs, N, sign);
+    __syncthreads();
+    a0 = warp_sum_u(a0);
+    a1 = warp_sum_u(a1);
+    if (lane_id() == 0) {
+      if (a0) atomicAdd(&s_cnt[0][s], static_cast<unsigned long long>(a0));
+      if (a1) atomicAdd(&s_cnt[1][s], static_cast<unsigned long long>(a1));
+    }
+  }
+  cfl = warp_max_u(cfl);
+  if (lane_id() == 0 && cfl) atomicMax(&s_cfl, cfl);
+  __syncthreads();
+  if (do_push) {
+    // --- secondary emission from the ions this CTA saw absorbed -----------
+    const int n_abs = s_abs_n;
+    if (n_abs > cap && threadIdx.x == 0) s_flag[1] = 1;
+    const int na = min(n_abs, cap);
+    const double dx = P->dx, dt = P->dt;
+    for (int r0 = 0; r0 < na; r0 += kThreads) {
+      const int r = r0 + threadIdx.x;
+      const bool act = r < na;
+      int nse = 0;
+      AbsRec rec;
+      rec.id = 0; rec.electrode = 0; rec.u = 0.0;
+      if (act) {
+        rec = my_abs[r];
+        const double v = __ddiv_rn(__dmul_rn(rec.u, dx), dt);
+        const double Eev = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(0.5, P->m_i), v), v), P->e);
+        nse = see_count(P, Eev, rec.id, step);
+        if (rec.electrode == 0) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_energy),
+                    static_cast<unsigned long long>(__double2ll_rn(Eev * 256.0)));
+          atomicAdd(reinterpret_cast<unsigned long long*>(&s_conv),
+                    static_cast<unsigned long long>(static_cast<long long>(nse)));
+        }
+        if (nse) atomicAdd(&s_emit[rec.electrode], static_cast<unsigned long long>(nse));
+      }
+      const int incl = warp_incl_scan(nse);
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned long long wbase = 0ULL;
+      if (lane_id() == 31 && tot > 0)
+        wbase = atomicAdd(reinterpret_cast<unsigned long long*>(&S->n_alloc[CP_SECONDARIES]),
+                          static_cast<unsigned long long>(tot));
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      if (act && nse > 0) {
+        float* xs = reinterpret_cast<float*>(S->xi[CP_SECONDARIES]);
+        float* us = reinterpret_cast<float*>(S->u[CP_SECONDARIES]);
+        const double pi = 3.14159265358979323846;
+        for (int j = 0; j < nse; ++j) {
+          const U64x4 wv = philox4x64_10(rec.id, static_cast<uint64_t>(step),
+                                         static_cast<uint64_t>(1 + j), 0, P->seed, kTagSee);
+          const double ua = u01(wv.w[0]), ub = u01(wv.w[1]), frac = u01(wv.w[2]);
+          const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
+          const double vse = P->see_vth * fabs(z);
+          const double use = vse * dt / dx;
+          const double xd = (rec.electrode == 0) ? use * frac : static_cast<double>(N) - use * frac;
+          const float xr = nudge_inside<float>(xd, N);
+          const float ur = static_cast<float>(rec.electrode == 0 ? use : -use);
+          const unsigned long long slot = wbase + static_cast<unsigned long long>(incl - nse + j);
+          if (slot < static_cast<unsigned long long>(P->cap[CP_SECONDARIES])) {
+            xs[slot] = xr;
+            us[slot] = ur;
+            deposit_nodes(nd, xr);
+          } else {
+            s_flag[1] = 1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (na > 0) {  // at most 4096 impacts x (floor(gamma_max) + 1) electrons: no 32-bit overflow
+      fold_nodes(nd, Gs, N, -1LL);
+      __syncthreads();
+    }
+
+    // --- beam ions entering at x = d during this step ----------------------
+    const int Bn = P->beam_per_step;
+    if (Bn > 0 && static_cast<int>(blockIdx.x) * kThreads < Bn) {
+      float* xs = reinterpret_cast<float*>(S->xi[CP_IONS]);
+      float* us = reinterpret_cast<float*>(S->u[CP_IONS]);
+      uint32_t* idw = S->id;
+      const uint32_t id0 = S->beam_id_base;
+      int sincef = 0;
+      for (int k0 = blockIdx.x * kThreads; k0 < Bn; k0 += gridDim.x * kThreads) {
+        const int kk = k0 + threadIdx.x;
+        const bool act = kk < Bn;
+        const unsigned ball = __ballot_sync(0xffffffffu, act);
+        unsigned long long wbase = 0ULL;
+        if (lane_id() == 0 && ball)
+          wbase = atomicAdd(reinterpret_cast<unsigned long long*>(&S->n_alloc[CP_IONS]),
+                            static_cast<unsigned long long>(__popc(ball)));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (act) {
+          const U64x4 wv = philox4x64_10(static_cast<uint64_t>(kk), static_cast<uint64_t>(step), 0,
+                                         0, P->seed, kTagBeam);
+          const double frac = u01(wv.w[0]);
+          const double Eb = (P->beam_mode == 0)
+                                ? P->beam_E_eV
+                                : P->beam_Emin_eV + (P->beam_Emax_eV - P->beam_Emin_eV) * u01(wv.w[1]);
+          const double v = sqrt(2.0 * Eb * P->e / P->m_i);
+          const double ub = v * dt / dx;
+          const float xr = nudge_inside<float>(static_cast<double>(N) - ub * frac, N);
+          const unsigned long long slot =
+              wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));
+          if (slot < static_cast<unsigned long long>(P->cap[CP_IONS])) {
+            xs[slot] = xr;
+            us[slot] = static_cast<float>(-ub);
+            idw[slot] = id0 + static_cast<uint32_t>(step * Bn + kk);
+            deposit_nodes(nd, xr);
+          } else {
+            s_flag[1] = 1;
+          }
+        }
+        if (++sincef == 4 * kFlushTiles) {  // 512 ions per pass: bounded node sums
+          __syncthreads();
+          fold_nodes(nd, Gs, N, 1LL);
+          __syncthreads();
+          sincef = 0;
+        }
+      }
+      __syncthreads();
+      fold_nodes(nd, Gs, N, 1LL);
+    }
+  }
+  __syncthreads();
+
+  // --- add this CTA's grid and tallies into the global ones ------------------
+  for (int kq = threadIdx.x; kq <= N; kq += kThreads) {
+    const long long g = Gs[kq];
+    if (g != 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&B.G[kq]), static_cast<unsigned long long>(g));
+  }
+  if (threadIdx.x == 0 && do_push) {
+    for (int e = 0; e < 2; ++e)
+      for (int s = 0; s < kSpecies; ++s)
+        if (s_cnt[e][s]) atomicAdd(&S->absorbed[e][s], s_cnt[e][s]);
+    if (s_emit[0]) atomicAdd(&S->emitted[0], s_emit[0]);
+    if (s_emit[1]) atomicAdd(&S->emitted[1], s_emit[1]);
+    const long long conv = static_cast<long long>(s_cnt[0][CP_IONS]) -
+                           static_cast<long long>(s_cnt[0][CP_ELECTRONS]) -
+                           static_cast<long long>(s_cnt[0][CP_SECONDARIES]) + s_conv;
+    if (conv) atomicAdd(reinterpret_cast<unsigned long long*>(&S->conv_count),
+                        static_cast<unsigned long long>(conv));
+    if (s_energy) atomicAdd(reinterpret_cast<unsigned long long*>(&S->ion_energy_q),
+                            static_cast<unsigned long long>(s_energy));
+    if (s_cfl) atomicMax(&S->max_cfl_bits, s_cfl);
+    if (blockIdx.x == 0 && P->beam_per_step > 0)
+      atomicAdd(&S->injected, static_cast<unsigned long long>(P->beam_per_step));
+    if (s_flag[1]) atomicCAS(&S->status, 0, CP_ERR_CAPACITY);
+  }
+}
+
+cudaError_t push_async_configure(size_t smem) {
+  return cudaFuncSetAttribute(k_push_async, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem));
+}
+
+cudaError_t push_async_occupancy(size_t smem, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push_async, kThreads, smem);
+}
+
+cudaError_t push_async_launch(const Bufs& B, int grid, size_t smem, cudaStream_t st, int do_push) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_push_async, B, do_push);
+}
+
+}  // namespace cpk
