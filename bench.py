@@ -55,7 +55,7 @@ def workload(name, seed, pairs=None):
     return cfg
 
 
-PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_gap_1d_fp32_large.md")
+PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_async_gap_1d_fp32_large.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2603_24010_gb300", "csrc", f)
                   for f in ("cp_push_async.cu", "cp_push.cu", "cp_common.cuh", "cp_device.cuh")]
 
@@ -618,7 +618,8 @@ def main():
         "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
                      "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": r["traffic"],
-                     "kernel": "k_push", "peak_source": r["peak_kind"],
+                     "kernel": "k_push_async" if r["cfg"]["precision"] == W.FP32 else "k_push",
+                     "peak_source": r["peak_kind"],
                      "avg_launch_ms": r["avg_launch_ms"], "launches_used": r["n_sel"],
                      "bytes_per_particle_step": r["bpp"],
                      "solve_avg_ms": r["kernel_ms"][1] / max(r["kernel_n"][1], 1),
