@@ -508,8 +508,8 @@ __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
     if (t >= 0 && static_cast<int>(lane_id()) == __ffs(m) - 1) atomicAdd(&hist[t], __popc(m));
   }
   __syncthreads();
-  int* bh = D.bhist + static_cast<long long>(blockIdx.x) * D.T;
-  for (int t = threadIdx.x; t < D.T; t += blockDim.x) bh[t] = hist[t];
+  const int G = gridDim.x;  // layout [tile][block]: each tile's counts contiguous
+  for (int t = threadIdx.x; t < D.T; t += blockDim.x) D.bhist[static_cast<long long>(t) * G + blockIdx.x] = hist[t];
 }
 
 // one block: tile totals and per-block offsets, tile segment starts (padded
@@ -579,8 +579,9 @@ __global__ void k2_tilescan(Dev2D* Dp, int s, int G) {
   const int t = blockIdx.x, T = D.T;
   const int per = (G + blockDim.x - 1) / blockDim.x;
   const int b0 = min(static_cast<int>(threadIdx.x) * per, G), b1 = min(b0 + per, G);
+  int* col = D.bhist + static_cast<long long>(t) * G;
   int loc = 0;
-  for (int b = b0; b < b1; ++b) loc += D.bhist[static_cast<long long>(b) * T + t];
+  for (int b = b0; b < b1; ++b) loc += col[b];
   int incl = loc;
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -593,9 +594,8 @@ __global__ void k2_tilescan(Dev2D* Dp, int s, int G) {
   for (int q = 0; q < w; ++q) base += wsum[q];
   int run = base + incl - loc;
   for (int b = b0; b < b1; ++b) {
-    int* p = D.bhist + static_cast<long long>(b) * T + t;
-    const int c = *p;
-    *p = run;
+    const int c = col[b];
+    col[b] = run;
     run += c;
   }
   if (threadIdx.x == blockDim.x - 1) D.tile_cnt[s * T + t] = base + incl;
@@ -608,14 +608,14 @@ __global__ void k2_bases(Dev2D* Dp, int s, int G) {
   const int* ts = D.tile_start + s * (D.T + 1);
   for (long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; q < n;
        q += static_cast<long long>(gridDim.x) * blockDim.x)
-    D.bhist[q] += ts[q % D.T];
+    D.bhist[q] += ts[q / G];
 }
 
 __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
   extern __shared__ int cur[];
   const Dev2D& D = *Dp;
-  const int* bh = D.bhist + static_cast<long long>(blockIdx.x) * D.T;
-  for (int t = threadIdx.x; t < D.T; t += blockDim.x) cur[t] = bh[t];
+  for (int t = threadIdx.x; t < D.T; t += blockDim.x)
+    cur[t] = D.bhist[static_cast<long long>(t) * gridDim.x + blockIdx.x];
   __syncthreads();
   const float* xs = reinterpret_cast<const float*>(S->xi[s]);
   const float* us = reinterpret_cast<const float*>(S->u[s]);
@@ -748,61 +748,150 @@ __global__ void k2_fwd(Dev2D* Dp, long long* G1) {
   for (int k = threadIdx.x; k <= Ny / 2; k += blockDim.x) R[k] = buf[k];
 }
 
-// One thread per mode k = 1..Ny/2: Thomas over i = 1..Nx-1 with phi = 0 at
+// One warp per mode k = 1..Ny/2: Thomas over i = 1..Nx-1 with phi = 0 at
 // both ends for  Phi_{i-1} - (2 + kappa_k) Phi_i + Phi_{i+1} = -dx^2 R_i / eps0.
 // The elimination factors depend on (i, k) only and are tabulated once
-// (k2_tables); a step runs the two substitutions, 16 rows of loads ahead.
-constexpr int kU2 = 16;
-__global__ void __launch_bounds__(64) k2_modes(Dev2D* Dp, float c_rhs) {
+// (k2_tables).  Both substitutions are first-order linear recurrences,
+// d_i = a_i d_{i-1} + b_i (a_i = -inv_i, b_i = c inv_i R_i) forward and
+// x_i = -c'_i x_{i+1} + d_i backward; each lane composes the affine map of
+// its segment of rows, a warp scan of the maps gives every segment its
+// incoming value, and the lanes then apply their segments.
+struct Aff {
+  float a;
+  float2 b;
+};
+
+__device__ __forceinline__ Aff aff_then(Aff f, Aff g) {  // g after f
+  Aff h;
+  h.a = g.a * f.a;
+  h.b = make_float2(fmaf(g.a, f.b.x, g.b.x), fmaf(g.a, f.b.y, g.b.y));
+  return h;
+}
+
+__device__ __forceinline__ Aff aff_shfl_up(Aff f, int o) {
+  Aff r;
+  r.a = __shfl_up_sync(0xffffffffu, f.a, o);
+  r.b.x = __shfl_up_sync(0xffffffffu, f.b.x, o);
+  r.b.y = __shfl_up_sync(0xffffffffu, f.b.y, o);
+  return r;
+}
+
+constexpr int kU2 = 8;  // rows of loads issued ahead
+
+__global__ void __launch_bounds__(128) k2_modes(Dev2D* Dp, float c_rhs) {
   const Dev2D& D = *Dp;
-  const int k = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int M = D.Ny / 2 + 1;
-  if (k >= M) return;
+  if (k >= M) return;  // whole warps leave together
+  const int lane = static_cast<int>(lane_id());
   float2* __restrict__ R = D.R;
   const float* __restrict__ inv = D.tinv;
   const float* __restrict__ cp = D.cp;
-  const int n = D.Nx - 1;  // rows 1..n
-  float2 d = make_float2(0.0f, 0.0f);
-  for (int i0 = 1; i0 <= n; i0 += kU2) {
-    float2 r[kU2];
+  const int n = D.Nx - 1;             // rows 1..n
+  const int seg = (n + 31) / 32;
+  const int r0 = 1 + lane * seg, r1 = min(n + 1, r0 + seg);  // this lane's rows [r0, r1)
+  // forward: compose this segment's map
+  Aff f;
+  f.a = 1.0f;
+  f.b = make_float2(0.0f, 0.0f);
+  for (int i0 = r0; i0 < r1; i0 += kU2) {
+    float2 rr[kU2];
     float iv[kU2];
 #pragma unroll
-    for (int q = 0; q < kU2; ++q) {
-      const int i = i0 + q;
-      if (i <= n) {
-        r[q] = R[static_cast<long long>(i) * M + k];
-        iv[q] = inv[static_cast<long long>(i) * M + k];
+    for (int q = 0; q < kU2; ++q)
+      if (i0 + q < r1) {
+        rr[q] = R[static_cast<long long>(i0 + q) * M + k];
+        iv[q] = inv[static_cast<long long>(i0 + q) * M + k];
       }
-    }
 #pragma unroll
-    for (int q = 0; q < kU2; ++q) {
-      const int i = i0 + q;
-      if (i <= n) {
-        d = make_float2((c_rhs * r[q].x - d.x) * iv[q], (c_rhs * r[q].y - d.y) * iv[q]);
-        R[static_cast<long long>(i) * M + k] = d;
+    for (int q = 0; q < kU2; ++q)
+      if (i0 + q < r1) {
+        Aff g;
+        g.a = -iv[q];
+        g.b = make_float2(c_rhs * iv[q] * rr[q].x, c_rhs * iv[q] * rr[q].y);
+        f = aff_then(f, g);
       }
-    }
   }
-  float2 x = make_float2(0.0f, 0.0f);
-  for (int i0 = n; i0 >= 1; i0 -= kU2) {
+  // exclusive scan over the lanes: the map from d_0 = 0 to this segment's start
+  Aff incl = f;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Aff y = aff_shfl_up(incl, o);
+    if (lane >= o) incl = aff_then(y, incl);
+  }
+  Aff ex = aff_shfl_up(incl, 1);
+  float2 d = (lane == 0) ? make_float2(0.0f, 0.0f) : ex.b;
+  // forward: apply
+  for (int i0 = r0; i0 < r1; i0 += kU2) {
+    float2 rr[kU2];
+    float iv[kU2];
+#pragma unroll
+    for (int q = 0; q < kU2; ++q)
+      if (i0 + q < r1) {
+        rr[q] = R[static_cast<long long>(i0 + q) * M + k];
+        iv[q] = inv[static_cast<long long>(i0 + q) * M + k];
+      }
+#pragma unroll
+    for (int q = 0; q < kU2; ++q)
+      if (i0 + q < r1) {
+        const float a = -iv[q];
+        d = make_float2(fmaf(a, d.x, c_rhs * iv[q] * rr[q].x), fmaf(a, d.y, c_rhs * iv[q] * rr[q].y));
+        R[static_cast<long long>(i0 + q) * M + k] = d;
+      }
+  }
+  // backward: x_i = -c'_i x_{i+1} + d_i, segments from the last row down
+  Aff g;
+  g.a = 1.0f;
+  g.b = make_float2(0.0f, 0.0f);
+  for (int i0 = r1 - 1; i0 >= r0; i0 -= kU2) {
     float2 dd[kU2];
     float cc[kU2];
 #pragma unroll
-    for (int q = 0; q < kU2; ++q) {
-      const int i = i0 - q;
-      if (i >= 1) {
-        dd[q] = R[static_cast<long long>(i) * M + k];
-        cc[q] = cp[static_cast<long long>(i) * M + k];
+    for (int q = 0; q < kU2; ++q)
+      if (i0 - q >= r0) {
+        dd[q] = R[static_cast<long long>(i0 - q) * M + k];
+        cc[q] = cp[static_cast<long long>(i0 - q) * M + k];
       }
-    }
 #pragma unroll
-    for (int q = 0; q < kU2; ++q) {
-      const int i = i0 - q;
-      if (i >= 1) {
-        x = make_float2(dd[q].x - cc[q] * x.x, dd[q].y - cc[q] * x.y);
-        R[static_cast<long long>(i) * M + k] = x;
+    for (int q = 0; q < kU2; ++q)
+      if (i0 - q >= r0) {
+        Aff h;
+        h.a = -cc[q];
+        h.b = dd[q];
+        g = aff_then(g, h);
       }
-    }
+  }
+  // reverse exclusive scan (lane 31 holds the last rows)
+  Aff incl2 = g;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Aff y;
+    y.a = __shfl_down_sync(0xffffffffu, incl2.a, o);
+    y.b.x = __shfl_down_sync(0xffffffffu, incl2.b.x, o);
+    y.b.y = __shfl_down_sync(0xffffffffu, incl2.b.y, o);
+    if (lane + o < 32) incl2 = aff_then(y, incl2);
+  }
+  float2 x;
+  {
+    const float bx = __shfl_down_sync(0xffffffffu, incl2.b.x, 1);
+    const float by = __shfl_down_sync(0xffffffffu, incl2.b.y, 1);
+    x = (lane == 31) ? make_float2(0.0f, 0.0f) : make_float2(bx, by);
+  }
+  for (int i0 = r1 - 1; i0 >= r0; i0 -= kU2) {
+    float2 dd[kU2];
+    float cc[kU2];
+#pragma unroll
+    for (int q = 0; q < kU2; ++q)
+      if (i0 - q >= r0) {
+        dd[q] = R[static_cast<long long>(i0 - q) * M + k];
+        cc[q] = cp[static_cast<long long>(i0 - q) * M + k];
+      }
+#pragma unroll
+    for (int q = 0; q < kU2; ++q)
+      if (i0 - q >= r0) {
+        x = make_float2(fmaf(-cc[q], x.x, dd[q].x), fmaf(-cc[q], x.y, dd[q].y));
+        R[static_cast<long long>(i0 - q) * M + k] = x;
+      }
   }
 }
 
@@ -928,7 +1017,7 @@ cudaError_t solve2_modes_launch(void* D, int Nx, int Ny, float c_rhs, const doub
                                 cudaStream_t st) {
   Dev2D* Dp = static_cast<Dev2D*>(D);
   const int M = Ny / 2;
-  k2_modes<<<(M + 63) / 64, 64, 0, st>>>(Dp, c_rhs);
+  k2_modes<<<(M + 3) / 4, 128, 0, st>>>(Dp, c_rhs);
   if (Nx > 1) k2_inv<<<Nx - 1, 256, sizeof(float2) * Ny, st>>>(Dp);
   const long long n = static_cast<long long>(Nx + 1) * Ny;
   const int grid = static_cast<int>(std::min<long long>((n + 255) / 256, 4096));
