@@ -497,15 +497,23 @@ __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
   block_range(S->n_proc[s], &b0, &b1);
   // warp-uniform trips; lanes of one tile (sorted data: most of a warp)
   // are counted by one shared-memory atomic
-  for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += blockDim.x) {
-    const long long k = k0 + lane_id();
-    int t = -1;
-    if (k < b1) {
-      const float x = xs[k];
-      if (x > 0.0f && x < D.Nxf) t = tile_of(D, x, ys[k]);
+  constexpr int U = 4;
+  const long long step = static_cast<long long>(blockDim.x) * U;
+  for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += step) {
+    float x[U], y[U];
+#pragma unroll
+    for (int c = 0; c < U; ++c) {
+      const long long k = k0 + static_cast<long long>(c) * blockDim.x + lane_id();
+      const bool in = k < b1;
+      x[c] = in ? xs[k] : -1.0f;
+      y[c] = in ? ys[k] : 0.0f;
     }
-    const unsigned m = __match_any_sync(0xffffffffu, t);
-    if (t >= 0 && static_cast<int>(lane_id()) == __ffs(m) - 1) atomicAdd(&hist[t], __popc(m));
+#pragma unroll
+    for (int c = 0; c < U; ++c) {
+      const int t = (x[c] > 0.0f && x[c] < D.Nxf) ? tile_of(D, x[c], y[c]) : -1;
+      const unsigned m = __match_any_sync(0xffffffffu, t);
+      if (t >= 0 && static_cast<int>(lane_id()) == __ffs(m) - 1) atomicAdd(&hist[t], __popc(m));
+    }
   }
   __syncthreads();
   const int G = gridDim.x;  // layout [tile][block]: each tile's counts contiguous
@@ -627,32 +635,41 @@ __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
   float* wd = reinterpret_cast<float*>(D.w_alt[s]);
   const uint32_t* is = S->id;
   uint32_t* id_d = S->id_alt;
+  const bool ions = (s == CP_IONS);
   long long b0, b1;
   block_range(S->n_proc[s], &b0, &b1);
-  for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += blockDim.x) {
-    const long long k = k0 + lane_id();
-    int t = -1;
-    float x = 0.0f, y = 0.0f;
-    if (k < b1) {
-      x = xs[k];
-      if (x > 0.0f && x < D.Nxf) {
-        y = ys[k];
-        t = tile_of(D, x, y);
-      }
+  constexpr int U = 4;  // warp chunks whose loads are issued together
+  const long long step = static_cast<long long>(blockDim.x) * U;
+  for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += step) {
+    float x[U], y[U], u[U], w[U];
+    uint32_t id[U];
+#pragma unroll
+    for (int c = 0; c < U; ++c) {  // every load first: one memory round trip per U chunks
+      const long long k = k0 + static_cast<long long>(c) * blockDim.x + lane_id();
+      const bool in = k < b1;
+      x[c] = in ? xs[k] : -1.0f;
+      y[c] = in ? ys[k] : 0.0f;
+      u[c] = in ? us[k] : 0.0f;
+      w[c] = in ? ws[k] : 0.0f;
+      id[c] = (in && ions) ? is[k] : 0u;
     }
-    const unsigned m = __match_any_sync(0xffffffffu, t);
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (t >= 0 && static_cast<int>(lane_id()) == leader) base = atomicAdd(&cur[t], __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (t < 0) continue;
-    const long long o = static_cast<long long>(base) + __popc(m & ((1u << lane_id()) - 1u));
-    if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
-    xd[o] = x;
-    ud[o] = us[k];
-    yd[o] = y;
-    wd[o] = ws[k];
-    if (s == CP_IONS) id_d[o] = is[k];
+#pragma unroll
+    for (int c = 0; c < U; ++c) {
+      const int t = (x[c] > 0.0f && x[c] < D.Nxf) ? tile_of(D, x[c], y[c]) : -1;
+      const unsigned m = __match_any_sync(0xffffffffu, t);
+      const int leader = __ffs(m) - 1;
+      int base = 0;
+      if (t >= 0 && static_cast<int>(lane_id()) == leader) base = atomicAdd(&cur[t], __popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (t < 0) continue;
+      const long long o = static_cast<long long>(base) + __popc(m & ((1u << lane_id()) - 1u));
+      if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
+      xd[o] = x[c];
+      ud[o] = u[c];
+      yd[o] = y[c];
+      wd[o] = w[c];
+      if (ions) id_d[o] = id[c];
+    }
   }
 }
 
