@@ -136,15 +136,6 @@ __device__ __forceinline__ void deposit2_global(const Dev2D& D, float x, float y
   if (w11) atomic_add_i64(&G[r1 + j1], sign * di1 * w11);
 }
 
-__device__ __forceinline__ void cp_async16_2d(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-               "l"(src)
-               : "memory");
-}
-
-constexpr size_t kRing2Bytes = 2 * 4 * kThreads2 * sizeof(float4);  // 64 KB
-
 // ---------------------------------------------------------------------------
 // k2_push
 // ---------------------------------------------------------------------------
@@ -161,7 +152,6 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
   __shared__ long long s_conv, s_energy;
   __shared__ unsigned int s_cfl;
 
-  extern __shared__ __align__(16) float4 ring[];  // [slot][x, y, u, w][thread]
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
   const Dev2D& D = *Dp;
@@ -239,30 +229,14 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
     const uint32_t* ids = S->id;
     const float kx = D.kx[half ? 0 : 1][s], ky = D.ky[half ? 0 : 1][s];
     const long long sign = (s == CP_IONS) ? 1LL : -1LL;
-    // each thread's 4 particles of sub-chunk j travel through its two ring
-    // slots (cp.async): sub-chunk j+1 is on its way while j is processed
-    const long long nsub = (p1 - p0 + kThreads2 * 4 - 1) / (kThreads2 * 4);
-    auto issue = [&](long long j) {
-      const long long b = p0 + j * (kThreads2 * 4) + static_cast<long long>(threadIdx.x) * 4;
-      float4* slot = ring + static_cast<int>(j & 1) * (4 * kThreads2) + threadIdx.x;
-      if (j < nsub && b < p1) {
-        cp_async16_2d(slot, xs + b);
-        cp_async16_2d(slot + kThreads2, ys + b);
-        cp_async16_2d(slot + 2 * kThreads2, us + b);
-        cp_async16_2d(slot + 3 * kThreads2, ws + b);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    issue(0);
-    for (long long jsub = 0; jsub < nsub; ++jsub) {
-      issue(jsub + 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-      const long long base = p0 + jsub * (kThreads2 * 4) + static_cast<long long>(threadIdx.x) * 4;
+    for (long long b0 = p0; b0 < p1; b0 += kThreads2 * 4) {
+      const long long base = b0 + static_cast<long long>(threadIdx.x) * 4;
       if (base < p1) {
-        const float4* slot = ring + static_cast<int>(jsub & 1) * (4 * kThreads2) + threadIdx.x;
-        const float4 xa = slot[0], ya = slot[kThreads2], ua = slot[2 * kThreads2], wa = slot[3 * kThreads2];
-        float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {ya.x, ya.y, ya.z, ya.w};
-        float uv[4] = {ua.x, ua.y, ua.z, ua.w}, wv[4] = {wa.x, wa.y, wa.z, wa.w};
+        float xv[4], uv[4], yv[4], wv[4];
+        load4(xs + base, xv);
+        load4(us + base, uv);
+        load4(ys + base, yv);
+        load4(ws + base, wv);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float x = xv[q];
@@ -345,7 +319,6 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         store4(ws + base, wv);
       }
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (win) {  // flush the deposit window into the int64 grid
       __syncthreads();
       for (int q = threadIdx.x; q < kW2 * kW2; q += kThreads2) {
@@ -1011,10 +984,7 @@ int kchunk2() { return kChunk2; }
 int tile2() { return kT2; }
 
 cudaError_t push2_occupancy(int* per_sm) {
-  const cudaError_t e = cudaFuncSetAttribute(k2_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kRing2Bytes));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k2_push, kThreads2, kRing2Bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k2_push, kThreads2, 0);
 }
 
 cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* abs, int abs_cap,
@@ -1022,7 +992,6 @@ cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* a
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kThreads2, 1, 1);
-  cfg.dynamicSmemBytes = kRing2Bytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
