@@ -167,6 +167,17 @@ def load_particles(cfg, seed):
     return xe, ue, xI, ui
 
 
+def reduce_over_ranks(ms, e2e_ms, psteps, e2e_psteps, device):
+    """Whole-job figures of independent replicas: the slowest rank's times
+    and the sum of the particle-steps of all ranks."""
+    import torch
+    t = torch.tensor([ms, e2e_ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    c = torch.tensor([psteps, e2e_psteps], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(c[0]), int(c[1])
+
+
 def run_native(args, rank, world):
     import torch
     from paper_2603_24010_gb300 import native
@@ -246,12 +257,7 @@ def run_native(args, rank, world):
     d2h = (K + 1) * ctypes.sizeof(native.cp_diag)
 
     if world > 1:
-        t = torch.tensor([ms, e2e_s * 1e3], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        c = torch.tensor([psteps, e2e_psteps], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
-        ms, e2e_ms = float(t[0]), float(t[1])
-        psteps, e2e_psteps = int(c[0]), int(c[1])
+        ms, e2e_ms, psteps, e2e_psteps = reduce_over_ranks(ms, e2e_s * 1e3, psteps, e2e_psteps, "cuda")
     else:
         e2e_ms = e2e_s * 1e3
     peak, peak_kind = measured_peaks()
@@ -518,6 +524,7 @@ def oracle_sample(cfg, K, Wm, budget_s, rate_guess=4e7):
     h = r.history()
     psteps = int(h["n_live"][Wm:Wm + K].sum())
     r.close()
+    oracle_sample.ms_per_step = 1e3 * dt / max(K, 1)
     desc = ("oracle (plain FP64 C, 1 thread) on the same workload sub-sampled to %d pairs and "
             "%d beam ions/step (fraction %.4g of the macroparticles, weights scaled), %d "
             "warm-up + %d timed steps, %.1f s, status %d" % (n_pairs, beam, frac, Wm, K, dt, rc))
@@ -574,7 +581,8 @@ def main():
             return
         value, desc = oracle_sample(cfg, args.steps, args.warmup, budget_s=120.0)
         line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": getattr(oracle_sample, "ms_per_step", None),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config, "impl": "reference",
                 "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
