@@ -366,6 +366,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   __shared__ SolveSlotC slotC;
   __shared__ double slotd;
   __shared__ double sc[40];
+  __shared__ unsigned long long tal[11];  // the push's tallies, read early
   __shared__ int s_stop;
 
   cudaGridDependencySynchronize();  // the push that deposited G has completed
@@ -401,6 +402,78 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     B.G[N] = 0;
   }
   __syncthreads();
+  // circuit row, first part (every rank evaluates the same scalars): the
+  // source, the BDF2 history, the circuit solve and the x = 0 row's
+  // right-hand side need no scan, so one thread of the last warp does them
+  // -- and reads the push's tallies for the commit -- while the CTA scans.
+  if (threadIdx.x == kSolveThreads - 32) {
+    const double qw = P->e * P->weight;
+    const long long conv = do_push ? ldcg(&S->conv_count) : 0LL;
+    const double Q1 = ldcg(&S->Qh[0]), Q2 = ldcg(&S->Qh[1]);
+    const double Q3 = ldcg(&S->Qh[2]);
+    // source and BDF2 history of the new level: precomputed by the previous
+    // solve except for the first solve of a run
+    double Vs, hist;
+    if (do_push) {
+      Vs = ldcg(&S->nxt_Vs);
+      hist = ldcg(&S->nxt_hist);
+    } else {
+      Vs = B.vs[ldcg(&S->level)];
+      const double Q4 = ldcg(&S->Qh[3]);
+      hist = P->L4dt2 * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) + P->R2dt * (4.0 * Q1 - Q2);
+    }
+    const double phi0_prev = ldcg(&S->phi0_last);
+    // learned weak scheme: the network's prediction of the plasma's change of
+    // C phi_0 over this step, used while its tracked error is within bound
+    const int pred_ready = (B.net != nullptr) ? ldcg(&S->pred_ready) : 0;
+    const double J_pred = pred_ready ? ldcg(&S->J_pred) : 0.0;
+    double J_used = 0.0;
+    if (mode == 2 && pred_ready && ldcg(&S->n_eval) >= kPredMinEval &&
+        ldcg(&S->err_avg) <= B.net->bound * ldcg(&S->J_avg))
+      J_used = J_pred;
+    double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
+    if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
+      if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
+        g = P->g_strict;
+        Qpart = g * (Vs + hist);
+        gam = P->gam_strict;
+        inv_den = P->inv_den_strict;
+      } else {
+        // weak (Sec. 2.4.3): the circuit alone, its load capacitor starting
+        // from phi_0^{n-1}: a21 Q - hist + phi_0^{n-1} + (Q - Q^{n-1} + J)/C = V_s
+        Qpart = (Vs + hist + (Q1 - J_used) * P->inv_C - phi0_prev) * P->g_weak;
+      }
+    }
+    const double Qconv = static_cast<double>(conv) * qw;
+    const double sigma_prev = ldcg(&S->sigma);
+    // x = 0 row: Eq. Poisson_BC2 (strict) / Eq. Poisson_BC3 (weak), with
+    // rho_0 dx^2 / (2 eps0) = alpha G_0 / 2 (G_0 is even: boundary doubling)
+    const double b0 = P->dx_eps0 * (sigma_prev + (Qconv + Qpart - Q1) * P->inv_A) +
+                      P->alpha * static_cast<double>(G0 / 2);
+    sc[0] = b0; sc[1] = gam; sc[2] = g; sc[3] = Qpart; sc[4] = Vs; sc[5] = hist;
+    sc[6] = Qconv; sc[7] = sigma_prev; sc[8] = Q1; sc[9] = Q2; sc[10] = Q3;
+    sc[12] = static_cast<double>(conv);
+    sc[15] = J_used;
+    sc[30] = J_pred;
+    sc[31] = static_cast<double>(pred_ready);
+    sc[32] = phi0_prev;
+    sc[35] = inv_den;
+    if (do_push) {  // the push's tallies, read before the commit clears them
+      sc[33] = static_cast<double>(ldcg(&S->emitted[0]));
+      sc[34] = static_cast<double>(ldcg(&S->ion_energy_q)) / 256.0;
+      for (int e = 0; e < 2; ++e)
+        for (int q = 0; q < kSpecies; ++q) tal[e * kSpecies + q] = ldcg(&S->absorbed[e][q]);
+      tal[6] = ldcg(&S->emitted[0]);
+      tal[7] = ldcg(&S->emitted[1]);
+      tal[8] = ldcg(&S->injected);
+      tal[9] = static_cast<unsigned long long>(ldcg(&S->ion_energy_q));
+      tal[10] = ldcg(&S->max_cfl_bits);
+    } else {
+      sc[33] = 0.0;
+      sc[34] = 0.0;
+      for (int q = 0; q < 11; ++q) tal[q] = 0ULL;
+    }
+  }
   // this thread's run of rows and its segment totals
   const int per = (m + kSolveThreads - 1) / kSolveThreads;
   const int r0 = min(static_cast<int>(threadIdx.x) * per, m);
@@ -467,70 +540,12 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   const __int128 U = s_U;
   // offset of everything before this thread's run: rank, then warp, then lane
   const Seg off = seg_then(seg_then(s_rank_off, bexcl), wexcl);
-  // circuit row (every rank evaluates the same scalars)
+  // circuit row, second part: the electrode potential needs the scan total U
   if (threadIdx.x == 0) {
-    const double dt = P->dt, dx = P->dx, A = P->area, eps0 = P->eps0;
-    const double qw = P->e * P->weight;
-    const long long conv = do_push ? ldcg(&S->conv_count) : 0LL;
-    const double Q1 = ldcg(&S->Qh[0]), Q2 = ldcg(&S->Qh[1]);
-    const double Q3 = ldcg(&S->Qh[2]);
-    // source and BDF2 history of the new level: precomputed by the previous
-    // solve (circuit_next) except for the first solve of a run
-    double Vs, hist;
-    if (do_push) {
-      Vs = ldcg(&S->nxt_Vs);
-      hist = ldcg(&S->nxt_hist);
-    } else {
-      Vs = B.vs[ldcg(&S->level)];
-      const double Q4 = ldcg(&S->Qh[3]);
-      hist = P->L4dt2 * (24.0 * Q1 - 22.0 * Q2 + 8.0 * Q3 - Q4) + P->R2dt * (4.0 * Q1 - Q2);
-    }
-    const double phi0_prev = ldcg(&S->phi0_last);
-    // learned weak scheme: the network's prediction of the plasma's change of
-    // C phi_0 over this step, used while its tracked error is within bound
-    const int pred_ready = (B.net != nullptr) ? ldcg(&S->pred_ready) : 0;
-    const double J_pred = pred_ready ? ldcg(&S->J_pred) : 0.0;
-    double J_used = 0.0;
-    if (mode == 2 && pred_ready && ldcg(&S->n_eval) >= kPredMinEval &&
-        ldcg(&S->err_avg) <= B.net->bound * ldcg(&S->J_avg))
-      J_used = J_pred;
-    double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
-    if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
-      if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
-        g = P->g_strict;
-        Qpart = g * (Vs + hist);
-        gam = P->gam_strict;
-        inv_den = P->inv_den_strict;
-      } else {
-        // weak (Sec. 2.4.3): the circuit alone, its load capacitor starting
-        // from phi_0^{n-1}: a21 Q - hist + phi_0^{n-1} + (Q - Q^{n-1} + J)/C = V_s
-        Qpart = (Vs + hist + (Q1 - J_used) * P->inv_C - phi0_prev) * P->g_weak;
-      }
-    }
-    const double Qconv = static_cast<double>(conv) * qw;
-    const double sigma_prev = ldcg(&S->sigma);
-    // x = 0 row: Eq. Poisson_BC2 (strict) / Eq. Poisson_BC3 (weak), with
-    // rho_0 dx^2 / (2 eps0) = alpha G_0 / 2 (G_0 is even: boundary doubling)
-    const double b0 = P->dx_eps0 * (sigma_prev + (Qconv + Qpart - Q1) * P->inv_A) +
-                      P->alpha * static_cast<double>(G0 / 2);
+    const double b0 = sc[0], gam = sc[1], inv_den = sc[35];
     const double phi0 = (static_cast<double>(N) * b0 + P->alpha * i128_to_double(U)) * inv_den;
-    (void)dt; (void)dx; (void)A; (void)eps0;
-    sc[0] = b0; sc[1] = gam; sc[2] = g; sc[3] = Qpart; sc[4] = Vs; sc[5] = hist;
-    sc[6] = Qconv; sc[7] = sigma_prev; sc[8] = Q1; sc[9] = Q2; sc[10] = Q3;
     const double D0 = b0 - gam * phi0;  // D_0 = x_0 - x_1
     sc[11] = D0;
-    sc[12] = static_cast<double>(conv);
-    sc[15] = J_used;
-    sc[30] = J_pred;
-    sc[31] = static_cast<double>(pred_ready);
-    sc[32] = phi0_prev;
-    if (do_push) {  // the push's tallies, read before the commit clears them
-      sc[33] = static_cast<double>(ldcg(&S->emitted[0]));
-      sc[34] = static_cast<double>(ldcg(&S->ion_energy_q)) / 256.0;
-    } else {
-      sc[33] = 0.0;
-      sc[34] = 0.0;
-    }
     sc[24] = D0 * P->inv_dx;        // E_0
     sc[25] = P->alpha * P->inv_dx;  // dE_i / dS'_i
   }
@@ -729,18 +744,17 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     d.Q_circ = Qn;
     d.V_source = sc[4];
     d.residual = eta;
-    d.ion_energy_eV = do_push ? static_cast<double>(S->ion_energy_q) / 256.0 : 0.0;
-    d.max_cfl = do_push ? static_cast<double>(__uint_as_float(S->max_cfl_bits)) : 0.0;
+    d.ion_energy_eV = static_cast<double>(static_cast<long long>(tal[9])) / 256.0;
+    d.max_cfl = static_cast<double>(__uint_as_float(static_cast<unsigned int>(tal[10])));
     d.J_hat = sc[15];
     long long nl[kSpecies];
     for (int s = 0; s < kSpecies; ++s) {
-      for (int e = 0; e < 2; ++e)
-        d.absorbed[e][s] = do_push ? static_cast<int64_t>(S->absorbed[e][s]) : 0;
+      for (int e = 0; e < 2; ++e) d.absorbed[e][s] = static_cast<int64_t>(tal[e * kSpecies + s]);
       nl[s] = S->n_live[s] - d.absorbed[0][s] - d.absorbed[1][s];
     }
-    d.emitted[0] = do_push ? static_cast<int64_t>(S->emitted[0]) : 0;
-    d.emitted[1] = do_push ? static_cast<int64_t>(S->emitted[1]) : 0;
-    d.injected = do_push ? static_cast<int64_t>(S->injected) : 0;
+    d.emitted[0] = static_cast<int64_t>(tal[6]);
+    d.emitted[1] = static_cast<int64_t>(tal[7]);
+    d.injected = static_cast<int64_t>(tal[8]);
     nl[1] += d.injected;
     nl[2] += d.emitted[0] + d.emitted[1];
     for (int s = 0; s < kSpecies; ++s) d.n_live[s] = nl[s];
