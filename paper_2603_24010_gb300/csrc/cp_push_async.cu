@@ -8,9 +8,10 @@
 // cp.async copies, so two tiles are always on their way while the third is
 // processed, without holding registers for them and without block-wide
 // synchronisation (each thread waits only for its own copy groups).  To make
-// room for the ring at two CTAs per SM, the field table keeps only the N
-// half-grid values (the slope is recomputed from neighbours exactly as the
-// solve forms it) and the deposit uses one 32-bit sum per node.
+// room for the ring at two CTAs per SM, the field table keeps only the
+// half-grid values, padded by a copy of each end value (the slope is
+// recomputed from neighbours exactly as the solve forms it, and is zero past
+// either end), and the deposit uses one 32-bit sum per node.
 #include "cp_common.cuh"
 
 namespace cpk {
@@ -43,41 +44,37 @@ __device__ __forceinline__ void fold_nodes(unsigned int* nd, long long* Gs, int 
   }
 }
 
-// CIC deposit of one particle into the node sums: node i gets 2^16 - W1, node i+1 W1
+// CIC deposit of one particle into the node sums: node i gets 2^16 - W1,
+// node i+1 W1, with i = floor(x) and W1 = floor(2^16 (x - i)).  x 2^16 is
+// exact (power-of-two scaling) and below 2^32 (the N + 1 node sums and the
+// field table take 8 B per cell of shared memory, so N < 2^16), so one
+// truncating conversion gives i in its high and W1 in its low 16 bits.
 __device__ __forceinline__ void deposit_nodes(unsigned int* nd, float x) {
-  const float fl = floorf(x);
-  const int i = static_cast<int>(fl);
-  const unsigned int w1 = frac_to_fix(x - fl);
+  const unsigned int F = __float2uint_rz(x * 65536.0f);
+  const unsigned int i = F >> 16;
+  const unsigned int w1 = F & 0xFFFFu;
   atomicAdd(&nd[i], 65536u - w1);
   atomicAdd(&nd[i + 1], w1);
 }
 
-// gather from the field table E[0..N-1] (E_{j+1/2}); the pair (E_j, slope)
-// of the pair table is formed here with the same FP32 subtraction
-__device__ __forceinline__ float gather_tab(const float* Et, int N, float x) {
+// gather from the padded field table Et[k] = E_{k-1/2} (k = 1..N), Et[0] =
+// E_{1/2}, Et[N+1] = E_{N-1/2}: the pair (E_{j+1/2}, slope) of the pair table
+// is formed here with the same FP32 subtraction, and the repeated end values
+// give the constant extension (slope +0) for j = -1 and j = N-1
+__device__ __forceinline__ float gather_tab(const float* Et, float x) {
   const float s = x - 0.5f;
   const float jf = floorf(s);
   const int j = static_cast<int>(jf);
   const float t = s - jf;
-  float e0, d;
-  if (j < 0) {
-    e0 = Et[0];
-    d = 0.0f;
-  } else if (j >= N - 1) {
-    e0 = Et[N - 1];
-    d = 0.0f;
-  } else {
-    e0 = Et[j];
-    d = Et[j + 1] - e0;
-  }
-  return fmaf(t, d, e0);
+  const float e0 = Et[j + 1];
+  return fmaf(t, Et[j + 2] - e0, e0);
 }
 
 constexpr size_t kRingBytes = static_cast<size_t>(kAStages) * kThreads * 32;
 
 size_t push_async_smem_bytes(int N) {
   return kRingBytes + align16(sizeof(long long) * (N + 1)) + align16(sizeof(unsigned int) * (N + 1)) +
-         align16(sizeof(float) * N);
+         align16(sizeof(float) * (N + 2));
 }
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int do_push) {
@@ -116,7 +113,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
   for (int k = threadIdx.x; k <= N; k += kThreads) {
     Gs[k] = 0;
     nd[k] = 0u;
-    if (k < N) Et[k] = Epair[k + 1].x;
+    const float e = Epair[k].x;  // pair 0 repeats E_{1/2}
+    Et[k] = e;
+    if (k == N) Et[N + 1] = e;
   }
   __syncthreads();
 
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     float* __restrict__ us = reinterpret_cast<float*>(S->u[s]);
     const int64_t n = S->n_proc[s];  // multiple of 4
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    const int64_t mine = (ntiles > blockIdx.x) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const int mine = (ntiles > blockIdx.x) ? static_cast<int>((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
     const long long sign = (s == CP_IONS) ? 1LL : -1LL;
     const float kap = P->kap_f[half ? 0 : 1][s];
     const uint32_t* ids = S->id;
@@ -140,23 +139,27 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     int since = 0;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kTile;
     const int64_t base0 = static_cast<int64_t>(blockIdx.x) * kTile + static_cast<int64_t>(threadIdx.x) * kPerThread;
-    auto issue = [&](int64_t j) {  // this thread's four particles of its j-th tile
-      const int64_t b = base0 + j * stride;
-      float4* slot = my_slot + static_cast<int>(j % kAStages) * kThreads * 2;
-      if (j < mine && b < n) {
-        cp_async16(slot, xs + b);
-        if (do_push) cp_async16(slot + kThreads, us + b);
+    int64_t b_next = base0;  // first particle of this thread's next tile to fetch
+    int st_next = 0;         // its ring slot
+    auto issue = [&](bool go) {  // this thread's four particles of its next tile
+      float4* slot = my_slot + st_next * (kThreads * 2);
+      if (go && b_next < n) {
+        cp_async16(slot, xs + b_next);
+        if (do_push) cp_async16(slot + kThreads, us + b_next);
       }
       cp_async_commit();
+      b_next += stride;
+      st_next = (st_next == kAStages - 1) ? 0 : st_next + 1;
     };
-    issue(0);
-    issue(1);
-    for (int64_t j = 0; j < mine; ++j) {
-      issue(j + 2);
+    issue(0 < mine);
+    issue(1 < mine);
+    int64_t base = base0;  // first particle of this thread's tile j
+    int st = 0;            // its ring slot
+    for (int j = 0; j < mine; ++j, base += stride, st = (st == kAStages - 1) ? 0 : st + 1) {
+      issue(j + 2 < mine);
       cp_async_wait<2>();  // this thread's copies of tile j have landed
-      const int64_t base = base0 + j * stride;
       if (base < n) {
-        const float4* slot = my_slot + static_cast<int>(j % kAStages) * kThreads * 2;
+        const float4* slot = my_slot + st * (kThreads * 2);
         const float4 xa = slot[0];
         float xv[4] = {xa.x, xa.y, xa.z, xa.w};
         if (do_push) {
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             if (xv[q] > 0.0f && xv[q] < Nr) {  // live (dead slots hold -1)
-              const float E = gather_tab(Et, N, xv[q]);
+              const float E = gather_tab(Et, xv[q]);
               const float un = fmaf(kap, E, uv[q]);
               const float xn = xv[q] + un;
               cfl = max(cfl, __float_as_uint(fabsf(un)));

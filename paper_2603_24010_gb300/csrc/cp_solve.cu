@@ -190,10 +190,18 @@ struct Seg {
   long long len;
 };
 
+// a b as a 128-bit integer from one 64 x 64 -> 128 product (no general
+// 128-bit multiplication)
+__device__ __forceinline__ __int128 mul_wide(long long a, long long b) {
+  const unsigned long long lo = static_cast<unsigned long long>(a) * static_cast<unsigned long long>(b);
+  const long long hi = __mul64hi(a, b);
+  return static_cast<__int128>((static_cast<unsigned __int128>(static_cast<unsigned long long>(hi)) << 64) | lo);
+}
+
 __device__ __forceinline__ Seg seg_then(const Seg& a, const Seg& b) {
   Seg r;
   r.s1 = a.s1 + b.s1;
-  r.s2 = a.s2 + b.s2 + static_cast<__int128>(b.len) * a.s1;
+  r.s2 = a.s2 + b.s2 + mul_wide(b.len, a.s1);
   r.len = a.len + b.len;
   return r;
 }
@@ -292,11 +300,10 @@ __device__ __forceinline__ void level_charges(const DevParams* P, const double* 
 // Predictor step on one CTA (all threads): append the feature row of the
 // level just solved to the 8-level window and, once the window is full,
 // evaluate the network for the next level's J_hat.
-__device__ __noinline__ void predictor_update(const Bufs& B, const double* sc, bool strict_rlc,
-                                              double phi0) {
-  const DevParams* P = B.P;
-  DevState* S = B.S;
-  const PredNet* net = B.net;
+// (The pointers are passed one by one: a reference to the kernel's parameter
+// block would force a copy of it into local memory for the whole solve.)
+__device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, const PredNet* net,
+                                              const double* sc, bool strict_rlc, double phi0) {
   __shared__ float x[kPredIn];
   __shared__ float h1[kHid], h2[kHid], h3[kHid];
   __shared__ float y[kPredOut];
@@ -717,7 +724,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   // rank's remote reads are done
   cl.barrier_wait(std::move(done_tok));
   if (rank == 1) {  // the predictor runs beside rank 0's commit
-    if (B.net != nullptr && do_push) predictor_update(B, sc, strict_rlc, phi0_fin);
+    if (B.net != nullptr && do_push) predictor_update(B.P, B.S, B.net, sc, strict_rlc, phi0_fin);
     return;
   }
   if (rank != 0) return;
@@ -811,7 +818,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   }
   if (nr == 1 && B.net != nullptr && do_push) {  // a one-CTA solve runs the predictor itself
     __syncthreads();
-    predictor_update(B, sc, strict_rlc, phi0_fin);
+    predictor_update(B.P, B.S, B.net, sc, strict_rlc, phi0_fin);
   }
 }
 
