@@ -439,7 +439,7 @@ void cp_batch_destroy(cp_batch* b);
  * cp_step_strict / cp_step_weak) and the other transverse Fourier modes
  * solve tridiagonal systems in x with phi = 0 on both electrodes.  The
  * particle store is kept sorted by 32 x 32-cell tiles, re-sorted every
- * sort_every steps (0 => 8).  FP32 particles only; n_cells_y a power of two
+ * sort_every steps (0 => 16).  FP32 particles only; n_cells_y a power of two
  * in 8..4096; n_cells <= 4096.
  * ------------------------------------------------------------------------ */
 typedef struct {

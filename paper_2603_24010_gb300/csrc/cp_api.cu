@@ -1295,7 +1295,7 @@ void cp_batch_destroy(cp_batch* b) {
 struct cp_gap2d {
   cp_ctx* c = nullptr;  // the 1D problem of the transverse mean (circuit, history)
   int Nx = 0, Ny = 0, T = 0, sms = 0, grid = 0;
-  int sort_every = 8, since_sort = 0;
+  int sort_every = 16, since_sort = 0;
   double ly = 0.0, beam_sigma = 0.0, beam_yc = 0.0;
   bool initialized = false;
   cpk::Dev2D hd{};             // host copy of the device struct
@@ -1612,7 +1612,7 @@ int cp2d_create(const cp_gap* gap, const cp_transverse* tr, const cp_circuit* ci
   g->ly = tr->length_y;
   g->beam_sigma = tr->beam_sigma;
   g->beam_yc = tr->beam_y0;
-  g->sort_every = tr->sort_every > 0 ? tr->sort_every : 8;
+  g->sort_every = tr->sort_every > 0 ? tr->sort_every : 16;
   *out = g;
   return CP_OK;
 }
