@@ -113,7 +113,7 @@ typedef struct {
   int64_t capacity[3]; /* particle store capacity per species */
   int64_t max_steps;   /* history rows to keep (levels 0..max_steps) */
   int32_t precision;   /* CP_FP64 or CP_FP32 */
-  int32_t compact_every; /* steps between removals of absorbed particles (0 => 64) */
+  int32_t compact_every; /* steps between removals of absorbed particles (0 => 128) */
 } cp_run;
 
 /* One diagnostics row per time level n (written by the solve at t_n). */
@@ -375,7 +375,8 @@ int cp_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t t,
 typedef struct cp_batch cp_batch;
 
 /* Create n instances (1 <= n <= 2048) from arrays of n parameter structs.
-   All runs share precision, max_steps and compact_every; n_cells <= 4096.
+   All runs share precision, max_steps and compact_every (0 => 64 here: the
+   small instances of an ensemble lose particles fast); n_cells <= 4096.
    Errors: CP_ERR_ARG, CP_ERR_OOM, CP_ERR_CUDA, and those of cp_create. */
 int cp_batch_create(int32_t n, const cp_gap* gaps, const cp_circuit* circuits,
                     const cp_see_beam* sees, const cp_run* runs, void* stream, cp_batch** out);
