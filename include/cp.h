@@ -76,7 +76,10 @@ typedef struct {
   double m_i;    /* ion mass [kg], singly charged */
   double weight; /* physical particles per macroparticle (all species) */
   double sigma0; /* surface charge density on x = 0 before the first step [C/m^2] */
-  int32_t n_cells; /* N >= 2; nodes 0..N */
+  int32_t n_cells; /* N >= 2; nodes 0..N.  At most what the push's shared
+                      memory holds: 11,390 cells with FP32 particles and
+                      7,231 with FP64 on a GB300 (227 KB per CTA); larger
+                      gaps are refused with CP_ERR_ARG */
   int32_t pad0;
 } cp_gap;
 

@@ -426,10 +426,20 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   if (!(gap->area > 0) && !(circ->C > 0)) return CP_ERR_ARG;
   cp_ctx* c = new (std::nothrow) cp_ctx();
   if (!c) return CP_ERR_OOM;
+  int smem_optin = 0;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) !=
+          cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
     return CP_ERR_CUDA;
+  }
+  // the push keeps the field table and the node sums of the whole gap in
+  // shared memory (1 KB left for its static variables)
+  if (cpk::push_smem_bytes(gap->n_cells, run->precision) + 1024 > static_cast<size_t>(smem_optin)) {
+    cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return CP_ERR_ARG;
   }
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   c->precision = run->precision;

@@ -75,6 +75,30 @@ def test_deposit_bit_exact_full_size_fp32(nat, orc):
     np.testing.assert_array_equal(g.grid()["G"], want)
 
 
+# ----------------------------------------------------------- largest gap
+@pytest.mark.parametrize("precision,n_cells", [(1, 11390), (0, 7231)])
+def test_largest_gap_that_fits(nat, orc, precision, n_cells):
+    """The largest gap whose field table and node sums fit the push's shared
+    memory (one push CTA per SM): bit-exact level-0 charge, then 20 coupled
+    steps against the oracle; one cell more is refused at creation."""
+    cfg = W.scaled(W.gap_1d_fp64(), n_cells=n_cells, n_pairs=40_003, beam_per_step=20)
+    g, r = load_both(nat, orc, cfg, precision, max_steps=30)
+    g.step(0, 0)
+    assert r.step(orc.STRICT, 0) == orc.OK
+    np.testing.assert_array_equal(g.grid()["G"], r.grid()["G"])
+    worst = 0.0
+    for k in range(20):
+        g.step(0, 1)
+        assert r.step(orc.STRICT, 1) == orc.OK
+        worst = max(worst, rel(g.grid()["E"], r.grid()["E"]))
+    # FP64 particles: rounding order only; FP32: the error of FP32 positions
+    assert worst < (1e-5 if precision == 0 else 2e-3), worst
+    if precision == 0:  # same absorption decisions
+        np.testing.assert_array_equal(g.history()["n_live"], r.history()["n_live"])
+    with pytest.raises(nat.CpError):
+        nat.Gap(dict(cfg, n_cells=n_cells + 1, precision=precision), max_steps=2)
+
+
 # ------------------------------------------------------------ particle-free
 def test_particle_free_gap_matches_oracle_and_closed_form(nat, orc):
     from closed_forms import rlc_closed_form
