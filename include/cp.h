@@ -395,6 +395,16 @@ int cp_batch_set_particles(cp_batch* b, int32_t i, int32_t species, const double
 int cp_batch_step_strict(cp_batch* b, int32_t n_steps, double residual_tol);
 int cp_batch_step_weak(cp_batch* b, int32_t n_steps);
 
+/* Learned weak coupling in an ensemble (Sec. 2.4.3 with the predicted
+   plasma term of cp_set_predictor): install a network on instance i (same
+   arguments and errors as cp_set_predictor, any time; each instance has its
+   own network and window), and advance every instance with the learned
+   weak scheme.  An instance without a network runs the plain weak scheme,
+   as cp_step_weak.  The ensemble's solve runs the network in the same CTA
+   after the commit; results are those of the instance's own context. */
+int cp_batch_set_predictor(cp_batch* b, int32_t i, const float* params, const cp_predictor* norm);
+int cp_batch_step_weak_learned(cp_batch* b, int32_t n_steps);
+
 /* Per-instance readers, as their single-context counterparts. */
 int cp_batch_read_history(cp_batch* b, int32_t i, int64_t first, int64_t n, cp_diag* out);
 int cp_batch_read_grid(cp_batch* b, int32_t i, double* phi, double* rho, double* E, int64_t* G,

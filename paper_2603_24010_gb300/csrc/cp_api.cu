@@ -895,8 +895,8 @@ struct cp_batch {
   int compact_every = 128;
   int since_compact = 0;
   int64_t max_steps = 0;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  double gtol[2] = {0.0, 0.0};
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // strict, weak, learned weak
+  double gtol[3] = {0.0, 0.0, 0.0};
   int64_t launches = 0;
   int* dstatus = nullptr;
   bool timing = false;
@@ -910,7 +910,7 @@ namespace {
 void batch_free(cp_batch* b) {
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   b->ev.clear();
-  for (int m = 0; m < 2; ++m)
+  for (int m = 0; m < 3; ++m)
     if (b->gexec[m]) cudaGraphExecDestroy(b->gexec[m]);
   cudaFree(b->dBall);
   cudaFree(b->abs);
@@ -940,7 +940,7 @@ int batch_set_shape(cp_batch* b, int threads, int per_sm_req) {
   }
   b->push_threads = threads;
   b->push_grid = grid;
-  for (int m = 0; m < 2; ++m) {  // graphs carry the old shape
+  for (int m = 0; m < 3; ++m) {  // graphs carry the old shape
     if (b->gexec[m]) cudaGraphExecDestroy(b->gexec[m]);
     b->gexec[m] = nullptr;
   }
@@ -1151,6 +1151,22 @@ int cp_batch_step_strict(cp_batch* b, int32_t n_steps, double residual_tol) {
 }
 
 int cp_batch_step_weak(cp_batch* b, int32_t n_steps) { return batch_steps(b, 1, n_steps, 1e300); }
+
+int cp_batch_set_predictor(cp_batch* b, int32_t i, const float* params, const cp_predictor* norm) {
+  if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;
+  const int rc = cp_set_predictor(b->inst[i], params, norm);
+  if (rc != CP_OK || !b->initialized) return rc;
+  // the ensemble kernels read the instance's buffer set from the device
+  // table at every launch: refresh instance i's entry
+  const cpk::Bufs hb = make_bufs(b->inst[i]);
+  CP_CUDA(cudaMemcpyAsync(b->dBall + i, &hb, sizeof(cpk::Bufs), cudaMemcpyHostToDevice, b->stream));
+  CP_CUDA(cudaStreamSynchronize(b->stream));
+  return CP_OK;
+}
+
+int cp_batch_step_weak_learned(cp_batch* b, int32_t n_steps) {
+  return batch_steps(b, 2, n_steps, 1e300);
+}
 
 int cp_batch_read_history(cp_batch* b, int32_t i, int64_t first, int64_t n, cp_diag* out) {
   if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;

@@ -28,7 +28,8 @@ EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "c
            "cp_step_weak_learned", "cp_predictor_samples", "cp_mlp_init", "cp_mlp_scales",
            "cp_mlp_normalize", "cp_mlp_forward", "cp_mlp_work_floats", "cp_mlp_loss_grad",
            "cp_mlp_adam", "cp_batch_create", "cp_batch_set_particles", "cp_batch_step_strict",
-           "cp_batch_step_weak", "cp_batch_read_history", "cp_batch_read_grid",
+           "cp_batch_step_weak", "cp_batch_set_predictor", "cp_batch_step_weak_learned",
+           "cp_batch_read_history", "cp_batch_read_grid",
            "cp_batch_get_particles", "cp_batch_status", "cp_batch_get_level",
            "cp_batch_last_launch_count", "cp_batch_set_launch", "cp_batch_get_launch",
            "cp_batch_autotune", "cp_batch_enable_timing", "cp_batch_read_timing",
@@ -136,6 +137,9 @@ def lib():
                                              C.c_int32]
         L.cp_batch_step_strict.argtypes = [vp, C.c_int32, C.c_double]
         L.cp_batch_step_weak.argtypes = [vp, C.c_int32]
+        L.cp_batch_set_predictor.argtypes = [vp, C.c_int32, C.POINTER(C.c_float),
+                                             C.POINTER(cp_predictor)]
+        L.cp_batch_step_weak_learned.argtypes = [vp, C.c_int32]
         L.cp_batch_read_history.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.POINTER(cp_diag)]
         L.cp_batch_read_grid.argtypes = [vp, C.c_int32, dp, dp, dp, i64p, C.c_int32]
         L.cp_batch_get_particles.argtypes = [vp, C.c_int32, C.c_int32, dp, dp, u32p, C.c_int64, i64p]
@@ -516,7 +520,17 @@ class Batch:
             return lib().cp_batch_step_strict(self.h, int(n_steps), float(tol))
         if mode == WEAK:
             return lib().cp_batch_step_weak(self.h, int(n_steps))
-        raise ValueError("the ensemble runs strict or weak coupling")
+        if mode == WEAK_LEARNED:
+            return lib().cp_batch_step_weak_learned(self.h, int(n_steps))
+        raise ValueError("unknown coupling mode %r" % (mode,))
+
+    def set_predictor(self, i, params, norm):
+        """Install a network on instance i (as Gap.set_predictor)."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_NPARAM:
+            raise ValueError("expected %d parameters" % MLP_NPARAM)
+        _check("cp_batch_set_predictor", lib().cp_batch_set_predictor(
+            self.h, int(i), p.ctypes.data_as(C.POINTER(C.c_float)), C.byref(norm)))
 
     def level_of(self, i):
         lv = C.c_int64()

@@ -4,8 +4,8 @@ Every instance of an ensemble must give bit for bit what it gives as a
 context of its own: the per-particle arithmetic is the same, the charge is
 integer, the draws are counter-based and the solve is an exact integer scan.
 Checked on instances of uneven size and physics (the ensemble workload,
-thinned), over enough steps for graph replays and removals, in strict and
-weak coupling, for every launch shape of the autotuner, and with one
+thinned), over enough steps for graph replays and removals, in strict,
+weak and learned weak coupling, for every launch shape of the autotuner, and with one
 instance stopping on a capacity error while the others go on.
 """
 import numpy as np
@@ -82,6 +82,54 @@ def check_same(native, b, i, ref):
     np.testing.assert_array_equal(gr["G"], ref["grid"]["G"])
     np.testing.assert_array_equal(gr["phi"], ref["grid"]["phi"])
     same_particles([b.particles(i, s) for s in range(3)], ref["parts"])
+
+
+def predictor_of(native, cfg):
+    """The hand-built persistence network (J^{n+1} = J^n) for an instance."""
+    import predictor_nets as PN
+    p, si, so = PN.persistence_net(cfg["C"], 1e-13)
+    nm = native.cp_predictor()
+    for f in range(5):
+        nm.in_scale[f] = float(si[f])
+    for o in range(2):
+        nm.out_scale[o] = float(so[o])
+    nm.bound = 0.5
+    return p, nm
+
+
+def test_learned_weak_ensemble_equals_single_instances(env):
+    """Learned weak coupling: each instance with its own network gives bit
+    for bit its single-context learned run (history including J_hat, grid,
+    particles); an instance left without a network runs plain weak."""
+    torch, native = env
+    cfgs = instances()
+    steps = 200
+    with_net = [i % 3 != 2 for i in range(len(cfgs))]
+    refs = []
+    for i, c in enumerate(cfgs):
+        g = native.Gap(c, max_steps=steps)
+        xi, ue, ui, ids = load(c)
+        g.set_particles(native.ELECTRONS, xi, ue)
+        g.set_particles(native.IONS, xi, ui, ids)
+        if with_net[i]:
+            g.set_predictor(*predictor_of(native, c))
+            rc = native.cp_step_weak_learned(g.ctx, steps)
+        else:
+            rc = native.cp_step_weak(g.ctx, steps)
+        refs.append(dict(rc=rc, h=g.history(), grid=g.grid(), parts=[g.particles(s) for s in range(3)]))
+        g.close()
+    b = batch_of(native, cfgs, steps)
+    for i, c in enumerate(cfgs):
+        if with_net[i]:
+            b.set_predictor(i, *predictor_of(native, c))
+    assert b.step(native.WEAK_LEARNED, steps) == native.OK
+    for i in range(len(cfgs)):
+        check_same(native, b, i, refs[i])
+        np.testing.assert_array_equal(b.history(i)["J_hat"], refs[i]["h"]["J_hat"])
+    b.close()
+    used = [int((r["h"]["J_hat"] != 0).sum()) for r in refs]
+    assert all(u == 0 for u, w in zip(used, with_net) if not w)
+    assert sum(used) > 100, used  # the learned path was exercised
 
 
 @pytest.mark.parametrize("mode", [0, 1])
