@@ -476,6 +476,16 @@ int cp2d_set_particles(cp_gap2d* g, int32_t species, const double* x, const doub
                        int32_t units);
 int cp2d_step_strict(cp_gap2d* g, int32_t n_steps, double residual_tol);
 int cp2d_step_weak(cp_gap2d* g, int32_t n_steps);
+
+/* Learned weak coupling of the transverse mean (the 1D coupled problem the
+   2D solve contains; Sec. 2.4.3 with the predicted plasma term): install a
+   network as cp_set_predictor does (its features are those of the mean:
+   convection charge, V_gap and surface-charge increments, emission and
+   absorbed ion energy at x = 0), and advance with the learned weak scheme.
+   Errors: as cp_set_predictor / cp2d_step_weak; CP_ERR_ARG if no network
+   is installed. */
+int cp2d_set_predictor(cp_gap2d* g, const float* params, const cp_predictor* norm);
+int cp2d_step_weak_learned(cp_gap2d* g, int32_t n_steps);
 /* Diagnostics rows (V_gap = phi on the driven electrode, circuit, tallies). */
 int cp2d_read_history(cp_gap2d* g, int64_t first, int64_t n, cp_diag* out);
 int cp2d_get_level(cp_gap2d* g, int64_t* level);

@@ -1688,6 +1688,16 @@ int cp2d_step_strict(cp_gap2d* g, int32_t n_steps, double residual_tol) {
 
 int cp2d_step_weak(cp_gap2d* g, int32_t n_steps) { return g2_steps(g, 1, n_steps, 1e300); }
 
+int cp2d_set_predictor(cp_gap2d* g, const float* params, const cp_predictor* norm) {
+  if (!g) return CP_ERR_ARG;
+  return cp_set_predictor(g->c, params, norm);  // the mean problem's context
+}
+
+int cp2d_step_weak_learned(cp_gap2d* g, int32_t n_steps) {
+  if (!g || !g->c->net) return CP_ERR_ARG;
+  return g2_steps(g, 2, n_steps, 1e300);
+}
+
 int cp2d_read_history(cp_gap2d* g, int64_t first, int64_t n, cp_diag* out) {
   if (!g) return CP_ERR_ARG;
   return cp_read_history(g->c, first, n, out);

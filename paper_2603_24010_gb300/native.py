@@ -34,7 +34,8 @@ EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "c
            "cp_batch_last_launch_count", "cp_batch_set_launch", "cp_batch_get_launch",
            "cp_batch_autotune", "cp_batch_enable_timing", "cp_batch_read_timing",
            "cp_batch_destroy", "cp2d_create", "cp2d_set_particles", "cp2d_step_strict",
-           "cp2d_step_weak", "cp2d_read_history", "cp2d_get_level", "cp2d_read_fields",
+           "cp2d_step_weak", "cp2d_set_predictor", "cp2d_step_weak_learned", "cp2d_read_history",
+           "cp2d_get_level", "cp2d_read_fields",
            "cp2d_get_particles", "cp2d_enable_timing", "cp2d_read_timing", "cp2d_last_launch_count",
            "cp2d_destroy", "cp_destroy", "cp_status_str")
 STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
@@ -159,6 +160,8 @@ def lib():
         L.cp2d_set_particles.argtypes = [vp, C.c_int32, dp, dp, dp, dp, u32p, C.c_int64, C.c_int32]
         L.cp2d_step_strict.argtypes = [vp, C.c_int32, C.c_double]
         L.cp2d_step_weak.argtypes = [vp, C.c_int32]
+        L.cp2d_set_predictor.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(cp_predictor)]
+        L.cp2d_step_weak_learned.argtypes = [vp, C.c_int32]
         L.cp2d_read_history.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(cp_diag)]
         L.cp2d_get_level.argtypes = [vp, i64p]
         L.cp2d_read_fields.argtypes = [vp, dp, C.POINTER(C.c_float), C.POINTER(C.c_float), i64p]
@@ -646,9 +649,19 @@ class Gap2D:
             rc = lib().cp2d_step_strict(self.h, int(n_steps), float(tol))
         elif mode == WEAK:
             rc = lib().cp2d_step_weak(self.h, int(n_steps))
+        elif mode == WEAK_LEARNED:
+            rc = lib().cp2d_step_weak_learned(self.h, int(n_steps))
         else:
-            raise ValueError("the 2D gap runs strict or weak coupling")
+            raise ValueError("unknown coupling mode %r" % (mode,))
         _check("cp2d_step", rc)
+
+    def set_predictor(self, params, norm):
+        """Install a network on the transverse mean (as Gap.set_predictor)."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_NPARAM:
+            raise ValueError("expected %d parameters" % MLP_NPARAM)
+        _check("cp2d_set_predictor", lib().cp2d_set_predictor(
+            self.h, p.ctypes.data_as(C.POINTER(C.c_float)), C.byref(norm)))
 
     @property
     def level(self):

@@ -133,6 +133,51 @@ def test_coupled_run_tracks_the_oracle(env, mode):
         np.testing.assert_allclose(hg[k], ho[k], rtol=0, atol=5e-3 * scale, err_msg=k)
 
 
+def test_learned_weak_coupling_of_the_mean(env):
+    """Learned weak coupling in 2D with the hand-built persistence network
+    (J_hat^{n+1} = J^n of the transverse mean): the network's prediction for
+    each level is the realised J of the level before (from the run's own
+    history), and with it the weak run tracks the strict one more closely
+    than the plain weak run."""
+    torch, native, gap2d = env
+    import predictor_nets as PN
+    cfg = cfg2d(64, 64, 8000, beam=24, gap=5e-4, see=8.0)
+    steps = 300
+    parts = loaded(cfg)
+    runs = {}
+    for mode in (0, 1):
+        g = gpu_gap(native, cfg, steps, mode=mode, parts=parts)
+        runs[mode] = g.history()
+        g.close()
+    hw = runs[1]
+    C = cfg["C"]
+    Jw = C * np.diff(hw["V_gap"]) - np.diff(hw["Q_circ"])  # J^n, n = 1..steps
+    S = float(np.abs(Jw).max()) / 10.0  # keeps the network in its linear range
+    p, si, so = PN.persistence_net(C, S)
+    nm = native.cp_predictor()
+    for f in range(5):
+        nm.in_scale[f] = float(si[f])
+    for o in range(2):
+        nm.out_scale[o] = float(so[o])
+    nm.bound = 0.5
+    g = native.Gap2D(cfg, max_steps=steps)
+    xi, eta, ue, we, ui, wi = parts
+    g.set_particles(native.ELECTRONS, xi, eta, ue, we)
+    g.set_particles(native.IONS, xi, eta, ui, wi, np.arange(xi.size, dtype=np.uint32))
+    g.set_predictor(p, nm)
+    g.step(native.WEAK_LEARNED, steps)
+    hl = g.history()
+    g.close()
+    used = hl["J_hat"] != 0
+    assert used.sum() > 200, used.sum()
+    J = C * np.diff(hl["V_gap"]) - np.diff(hl["Q_circ"])  # J[k] = J^{k+1}
+    n = np.nonzero(used[2:])[0] + 2  # levels n with a prediction, n >= 2
+    np.testing.assert_allclose(hl["J_hat"][n], J[n - 2], rtol=0, atol=1e-3 * np.abs(J).max())
+    hs = runs[0]
+    err = lambda h: np.abs(h["V_gap"] - hs["V_gap"]).max() / np.abs(hs["V_gap"]).max()
+    assert err(hl) < err(hw), (err(hl), err(hw))
+
+
 def test_results_do_not_depend_on_the_sort_interval(env):
     torch, native, gap2d = env
     cfg = cfg2d(64, 64, 60000, beam=40, gap=5e-4, see=4.0)
