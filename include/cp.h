@@ -405,6 +405,11 @@ int cp_batch_step_weak(cp_batch* b, int32_t n_steps);
 int cp_batch_set_predictor(cp_batch* b, int32_t i, const float* params, const cp_predictor* norm);
 int cp_batch_step_weak_learned(cp_batch* b, int32_t n_steps);
 
+/* Training samples of instance i, as cp_predictor_samples: an ensemble of
+   strict runs generates the predictor's training set in one pass. */
+int cp_batch_predictor_samples(cp_batch* b, int32_t i, int64_t first_level, int64_t n, float* X,
+                               float* Y);
+
 /* Per-instance readers, as their single-context counterparts. */
 int cp_batch_read_history(cp_batch* b, int32_t i, int64_t first, int64_t n, cp_diag* out);
 int cp_batch_read_grid(cp_batch* b, int32_t i, double* phi, double* rho, double* E, int64_t* G,

@@ -1168,6 +1168,12 @@ int cp_batch_step_weak_learned(cp_batch* b, int32_t n_steps) {
   return batch_steps(b, 2, n_steps, 1e300);
 }
 
+int cp_batch_predictor_samples(cp_batch* b, int32_t i, int64_t first_level, int64_t n, float* X,
+                               float* Y) {
+  if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;
+  return cp_predictor_samples(b->inst[i], first_level, n, X, Y);
+}
+
 int cp_batch_read_history(cp_batch* b, int32_t i, int64_t first, int64_t n, cp_diag* out) {
   if (!b || i < 0 || i >= b->E) return CP_ERR_ARG;
   return cp_read_history(b->inst[i], first, n, out);

@@ -29,6 +29,7 @@ EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "c
            "cp_mlp_normalize", "cp_mlp_forward", "cp_mlp_work_floats", "cp_mlp_loss_grad",
            "cp_mlp_adam", "cp_batch_create", "cp_batch_set_particles", "cp_batch_step_strict",
            "cp_batch_step_weak", "cp_batch_set_predictor", "cp_batch_step_weak_learned",
+           "cp_batch_predictor_samples",
            "cp_batch_read_history", "cp_batch_read_grid",
            "cp_batch_get_particles", "cp_batch_status", "cp_batch_get_level",
            "cp_batch_last_launch_count", "cp_batch_set_launch", "cp_batch_get_launch",
@@ -141,6 +142,8 @@ def lib():
         L.cp_batch_set_predictor.argtypes = [vp, C.c_int32, C.POINTER(C.c_float),
                                              C.POINTER(cp_predictor)]
         L.cp_batch_step_weak_learned.argtypes = [vp, C.c_int32]
+        L.cp_batch_predictor_samples.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.c_void_p,
+                                                 C.c_void_p]
         L.cp_batch_read_history.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, C.POINTER(cp_diag)]
         L.cp_batch_read_grid.argtypes = [vp, C.c_int32, dp, dp, dp, i64p, C.c_int32]
         L.cp_batch_get_particles.argtypes = [vp, C.c_int32, C.c_int32, dp, dp, u32p, C.c_int64, i64p]
@@ -484,13 +487,14 @@ def diag_to_dict(arr):
 class Batch:
     """An ensemble of independent gap instances driven through the cp_batch_* calls."""
 
-    def __init__(self, cfgs, max_steps, compact_every=0, stream=None):
+    def __init__(self, cfgs, max_steps, compact_every=0, stream=None, capacity=(0, 0, 0)):
         n = len(cfgs)
         self.cfgs = [dict(c) for c in cfgs]
         self.n = n
         gaps, circs, sees, runs = (cp_gap * n)(), (cp_circuit * n)(), (cp_see_beam * n)(), (cp_run * n)()
         for i, cfg in enumerate(cfgs):
-            g, c, s, r = structs_from_config(cfg, max_steps=max_steps, compact_every=compact_every)
+            g, c, s, r = structs_from_config(cfg, capacity=capacity, max_steps=max_steps,
+                                             compact_every=compact_every)
             gaps[i], circs[i], sees[i], runs[i] = g, c, s, r
         h = C.c_void_p()
         _check("cp_batch_create", lib().cp_batch_create(
@@ -526,6 +530,11 @@ class Batch:
         if mode == WEAK_LEARNED:
             return lib().cp_batch_step_weak_learned(self.h, int(n_steps))
         raise ValueError("unknown coupling mode %r" % (mode,))
+
+    def predictor_samples(self, i, first_level, n, X, Y):
+        """Instance i's training samples into device arrays X (n x 40), Y (n x 2)."""
+        _check("cp_batch_predictor_samples", lib().cp_batch_predictor_samples(
+            self.h, int(i), int(first_level), int(n), C.c_void_p(X), C.c_void_p(Y)))
 
     def set_predictor(self, i, params, norm):
         """Install a network on instance i (as Gap.set_predictor)."""

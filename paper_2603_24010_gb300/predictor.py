@@ -5,9 +5,10 @@ and time step runs in the library's kernels through the C ABI
 (``cp_predictor_samples``, ``cp_mlp_*``, ``cp_step_*``); PyTorch supplies the
 device buffers and the stream.
 
-Data: strict-coupling runs of a workload family (one Gap per seed).  Each
-run of S steps gives S - 8 samples: the 8-level feature window ending at
-level L and the targets of level L+1.
+Data: strict-coupling runs of a workload family, one Gap per seed
+(``strict_samples``) or one ensemble of all seeds advanced together
+(``ensemble_strict_samples``).  Each run of S steps gives S - 8 samples: the
+8-level feature window ending at level L and the targets of level L+1.
 """
 import time
 
@@ -51,6 +52,78 @@ def strict_samples(cfg, steps=None):
     torch.cuda.synchronize()
     g.close()
     return X, Y
+
+
+def load_batch(cfgs, steps, capacity=(0, 0, 0)):
+    """An ensemble of the workloads with their pairs loaded."""
+    b = native.Batch(cfgs, max_steps=steps, capacity=capacity)
+    for i, cfg in enumerate(cfgs):
+        xi, ue, ui = W.load_pairs(cfg)
+        prec = cfg.get("precision", W.FP64)
+        xe, ue = W.as_precision(xi, ue, cfg["n_cells"], prec)
+        xo, ui = W.as_precision(xi, ui, cfg["n_cells"], prec)
+        b.set_particles(i, native.ELECTRONS, xe, ue)
+        b.set_particles(i, native.IONS, xo, ui, np.arange(xi.size, dtype=np.uint32))
+    return b
+
+
+def _step_batch(b, mode, n):
+    rc = b.step(mode, n)
+    if rc != native.OK:
+        raise native.CpError("cp_batch_step", rc)
+
+
+def ensemble_strict_samples(cfgs, steps=None, capacity=(0, 0, 0)):
+    """Advance all runs together as one strict-coupling ensemble; return the
+    samples of every run, concatenated, on the device."""
+    torch = _torch()
+    steps = int(steps or cfgs[0]["steps"])
+    b = load_batch(cfgs, steps, capacity)
+    _step_batch(b, native.STRICT, steps)
+    n = steps - native.PRED_WINDOW  # windows ending at levels 8..steps-1
+    X = torch.empty((len(cfgs) * n, native.MLP_IN), dtype=torch.float32, device="cuda")
+    Y = torch.empty((len(cfgs) * n, native.MLP_OUT), dtype=torch.float32, device="cuda")
+    for i in range(len(cfgs)):
+        b.predictor_samples(i, native.PRED_WINDOW, n, X[i * n:].data_ptr(), Y[i * n:].data_ptr())
+    torch.cuda.synchronize()
+    b.close()
+    return X, Y
+
+
+def ensemble_evaluate(cfgs, params, norm, steps=None, capacity=(0, 0, 0),
+                      modes=(native.STRICT, native.WEAK, native.WEAK_LEARNED)):
+    """Every run under each scheme, as one ensemble per scheme (the network
+    installed on every instance); V_gap(t) and J_hat histories (runs x
+    levels) and the ensemble's wall time per step."""
+    torch = _torch()
+    steps = int(steps or cfgs[0]["steps"])
+    out = {}
+    for mode in modes:
+        b = load_batch(cfgs, steps, capacity)
+        if params is not None:
+            for i in range(len(cfgs)):
+                b.set_predictor(i, params, norm)
+        _step_batch(b, mode, 1)  # level 0 solve and first push outside the timing
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _step_batch(b, mode, steps - 1)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        hs = [b.history(i) for i in range(len(cfgs))]
+        b.close()
+        out[mode] = dict(V_gap=np.stack([h["V_gap"] for h in hs]),
+                         J_hat=np.stack([h["J_hat"] for h in hs]),
+                         ms_per_step=1e3 * wall / (steps - 1))
+    return out
+
+
+def ensemble_vgap_errors(res):
+    """Per run: max_t |V_gap - V_gap(strict)| / max_t |V_gap(strict)| of the
+    weak schemes."""
+    Vs = res[native.STRICT]["V_gap"]
+    scale = np.abs(Vs).max(axis=1)
+    return {mode: np.abs(res[mode]["V_gap"] - Vs).max(axis=1) / scale
+            for mode in (native.WEAK, native.WEAK_LEARNED) if mode in res}
 
 
 def train(X, Y, iters=3000, batch=8192, lr=2e-3, lr_final=1e-4, seed=0, bound=0.5):

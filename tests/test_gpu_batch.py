@@ -132,6 +132,34 @@ def test_learned_weak_ensemble_equals_single_instances(env):
     assert sum(used) > 100, used  # the learned path was exercised
 
 
+def test_ensemble_training_samples_equal_single_runs(env):
+    """The predictor's training samples read from an ensemble of strict runs
+    are those of the same runs as contexts of their own, bit for bit."""
+    torch, native = env
+    cfgs = instances(n=3)
+    steps = 120
+    n = steps - native.PRED_WINDOW
+    b = batch_of(native, cfgs, steps)
+    assert b.step(native.STRICT, steps) == native.OK
+    for i, cfg in enumerate(cfgs):
+        Xb = torch.empty((n, native.MLP_IN), dtype=torch.float32, device="cuda")
+        Yb = torch.empty((n, native.MLP_OUT), dtype=torch.float32, device="cuda")
+        b.predictor_samples(i, native.PRED_WINDOW, n, Xb.data_ptr(), Yb.data_ptr())
+        g = native.Gap(cfg, max_steps=steps)
+        xi, ue, ui, ids = load(cfg)
+        g.set_particles(native.ELECTRONS, xi, ue)
+        g.set_particles(native.IONS, xi, ui, ids)
+        assert native.cp_step_strict(g.ctx, steps, 1e-12) == native.OK
+        Xs = torch.empty_like(Xb)
+        Ys = torch.empty_like(Yb)
+        assert native.cp_predictor_samples(g.ctx, native.PRED_WINDOW, n, Xs.data_ptr(),
+                                           Ys.data_ptr()) == native.OK
+        torch.cuda.synchronize()
+        g.close()
+        assert torch.equal(Xb, Xs) and torch.equal(Yb, Ys)
+    b.close()
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ensemble_equals_single_instances(env, mode):
     torch, native = env
