@@ -10,13 +10,14 @@ that step / timed seconds.  Prints one JSON line.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
 After the timed run (outside it), the learned weak-coupling predictor is
-trained on strict runs of the same gap distribution and the V_gap(t) error of
-plain and learned weak coupling against strict is reported on held-out seeds
-("coupling"; skip with --no-coupling).
+trained on 2048 strict runs of the same gap distribution (generated as one
+ensemble) and the V_gap(t) error of plain and learned weak coupling against
+strict is reported on 256 held-out seeds ("coupling"; skip with
+--no-coupling).
 
-``--impl reference`` times the FP64 CPU oracle (the reference implementation
-of this build, written from the paper) on the host cores on a bounded sample
-of the same workload.
+``--impl reference`` times the FP64 CPU oracle (the plain implementation
+written from the paper) on the host cores on a bounded sample of the same
+workload.
 """
 import argparse
 import ctypes
