@@ -1,0 +1,47 @@
+"""Host-side logic that needs no GPU: the workload families the benchmark
+and the predictor study draw from, and the predictor driver's error
+summary.  (The kernels are covered by the -m gpu tests.)"""
+import numpy as np
+import pytest
+
+from paper_2603_24010_gb300 import workloads as W
+
+
+def test_thinned_gap_keeps_the_charge_of_the_full_gap():
+    """factor x fewer macroparticles of factor x the weight: the same plasma
+    density and beam current as the large gap, for every seed."""
+    for seed in range(4):
+        full = W.gap_1d_fp32_large(seed)
+        for f in (25, 100):
+            t = W.gap_1d_fp32_thinned(seed, factor=f)
+            assert t["n_pairs"] * t["weight"] == pytest.approx(full["n_pairs"] * full["weight"], rel=1e-12)
+            assert t["beam_per_step"] * f == full["beam_per_step"]
+            assert t["beam_mode"] == full["beam_mode"]  # same seed-drawn physics
+            for k in ("n_cells", "d", "dt", "C", "V0", "area"):
+                assert t[k] == full[k], k
+
+
+def test_ensemble_instances_are_seeded_and_uneven():
+    a = W.ensemble(64, seed=3, steps=10, thin=100)
+    b = W.ensemble(64, seed=3, steps=10, thin=100)
+    assert [x["n_cells"] for x in a] == [x["n_cells"] for x in b]
+    assert len({x["n_cells"] for x in a}) > 10  # uneven grids
+    assert all(256 <= x["n_cells"] <= 4096 for x in a)
+    assert all(x["see_scale"] == 0.0 for i, x in enumerate(a) if i % 8 == 7)
+    # each instance is a capacitor C = eps0 A / d when particle-free
+    for x in a:
+        assert x["C"] == pytest.approx(x["eps0"] * x["area"] / x["d"], rel=1e-12)
+
+
+def test_ensemble_vgap_errors_summary():
+    """Per run: max_t |V - V_strict| / max_t |V_strict| of each weak scheme."""
+    from paper_2603_24010_gb300 import native, predictor as PR
+    t = np.linspace(0.0, 1.0, 50)
+    Vs = np.stack([np.sin(3 * t) * (k + 1) for k in range(3)])
+    res = {native.STRICT: {"V_gap": Vs},
+           native.WEAK: {"V_gap": Vs + 0.01},
+           native.WEAK_LEARNED: {"V_gap": Vs * (1 + 1e-4)}}
+    err = PR.ensemble_vgap_errors(res)
+    scale = np.abs(Vs).max(axis=1)
+    np.testing.assert_allclose(err[native.WEAK], 0.01 / scale)
+    np.testing.assert_allclose(err[native.WEAK_LEARNED], 1e-4, rtol=1e-9)
