@@ -610,11 +610,12 @@ def main():
             torch.distributed.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle is timed beside one GPU only
         v, desc = oracle_sample(cfg, 200, 3, budget_s=20.0)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                "sample": desc}
-    coupling = None if args.no_coupling else run_coupling(args)
+    # the predictor study is a single-GPU experiment: replica runs skip it
+    coupling = None if (args.no_coupling or world > 1) else run_coupling(args)
     K = args.steps
     value = r["psteps"] / (r["ms"] * 1e-3)
     line = {
