@@ -451,17 +451,26 @@ def gap2d_main(args, config):
 # ---------------------------------------------------------------- coupling
 def run_coupling(args):
     """The learned weak-coupling predictor on the large gap's distribution:
-    an ensemble of strict runs generates the training set, the network is
-    trained, and on held-out seeds (one ensemble per scheme) the V_gap(t)
-    error of plain and learned weak coupling against strict and the wall
-    time of the three schemes are compared."""
+    an ensemble of thinned strict runs plus a few full-size strict runs
+    generate the training set, the network is trained, and on held-out seeds
+    (thinned: one ensemble per scheme; full-size: one run per scheme) the
+    V_gap(t) error of plain and learned weak coupling against strict and the
+    wall time of the three schemes are compared."""
     import torch
     from paper_2603_24010_gb300 import native
     from paper_2603_24010_gb300 import predictor as PR
     S, f = args.coupling_steps, args.coupling_factor
     fam = lambda seed: W.gap_1d_fp32_thinned(seed, factor=f, steps=S)  # noqa: E731
+    big = lambda seed: dict(W.gap_1d_fp32_large(seed), steps=S)  # noqa: E731
     t0 = time.perf_counter()
     X, Y = PR.ensemble_strict_samples([fam(1000 + k) for k in range(args.coupling_train)], S)
+    Xf, Yf = [X], [Y]
+    for k in range(args.coupling_train_full):
+        xk, yk = PR.strict_samples(big(3000 + k), S)
+        Xf.append(xk)
+        Yf.append(yk)
+    X, Y = torch.cat(Xf), torch.cat(Yf)
+    del Xf, Yf
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -472,18 +481,29 @@ def run_coupling(args):
     torch.cuda.empty_cache()
     t0 = time.perf_counter()
     res = PR.ensemble_evaluate([fam(2000 + k) for k in range(args.coupling_eval)], params, norm, S)
-    t_eval = time.perf_counter() - t0
     errs = PR.ensemble_vgap_errors(res)
     used = (res[native.WEAK_LEARNED]["J_hat"] != 0).mean(axis=1)
+    full = []
+    for k in range(args.coupling_eval_full):
+        rk = PR.evaluate(big(2000 + k), params, norm, S)
+        ek = PR.vgap_errors(rk)
+        full.append({"seed": 2000 + k, "vgap_err_weak": ek[native.WEAK],
+                     "vgap_err_learned": ek[native.WEAK_LEARNED],
+                     "predictor_used_frac": float((rk[native.WEAK_LEARNED]["J_hat"] != 0).mean()),
+                     "ms_per_step": {"strict": rk[native.STRICT]["ms_per_step"],
+                                     "weak": rk[native.WEAK]["ms_per_step"],
+                                     "weak_learned": rk[native.WEAK_LEARNED]["ms_per_step"]}})
+    t_eval = time.perf_counter() - t0
     cfg = fam(2000)
     return {
         "workload": ("gap_1d_fp32_thinned: the large gap's distribution (4096 cells, seed-drawn "
                      "beam mode) with %d x fewer, heavier macroparticles: %d pairs, %d beam "
-                     "ions/step, dt %.3g s, %d steps" % (f, cfg["n_pairs"], cfg["beam_per_step"],
-                                                         cfg["dt"], S)),
-        "train_runs": args.coupling_train, "eval_runs": args.coupling_eval,
-        "data": "training runs generated as one strict ensemble; each scheme evaluated as one "
-                "ensemble of the held-out seeds",
+                     "ions/step, dt %.3g s, %d steps; plus full-size runs of the large gap"
+                     % (f, cfg["n_pairs"], cfg["beam_per_step"], cfg["dt"], S)),
+        "train_runs": args.coupling_train, "train_runs_full_size": args.coupling_train_full,
+        "eval_runs": args.coupling_eval, "eval_runs_full_size": args.coupling_eval_full,
+        "data": "thinned training runs generated as one strict ensemble, full-size ones one by "
+                "one; thinned held-out seeds evaluated as one ensemble per scheme",
         "samples": n_samples, "train_iters": args.coupling_iters,
         "loss_first_last": [losses[0], losses[-1]],
         "metric": "max_t |V_gap - V_gap(strict)| / max_t |V_gap(strict)|, mean over eval seeds",
@@ -496,6 +516,7 @@ def run_coupling(args):
         "ms_per_step_ensemble": {"strict": res[native.STRICT]["ms_per_step"],
                                  "weak": res[native.WEAK]["ms_per_step"],
                                  "weak_learned": res[native.WEAK_LEARNED]["ms_per_step"]},
+        "full_size": full,
         "seconds": {"data": t_data, "train": t_train, "eval": t_eval},
     }
 
@@ -551,6 +572,10 @@ def main():
                     help="skip the learned-vs-plain weak coupling comparison")
     ap.add_argument("--coupling-train", type=int, default=2048)
     ap.add_argument("--coupling-eval", type=int, default=256)
+    ap.add_argument("--coupling-train-full", type=int, default=16,
+                    help="full-size strict training runs added to the thinned ones")
+    ap.add_argument("--coupling-eval-full", type=int, default=2,
+                    help="full-size held-out seeds evaluated one run per scheme")
     ap.add_argument("--coupling-steps", type=int, default=20000)
     ap.add_argument("--coupling-factor", type=int, default=100)
     ap.add_argument("--coupling-iters", type=int, default=6000)
