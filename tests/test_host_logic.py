@@ -45,3 +45,52 @@ def test_ensemble_vgap_errors_summary():
     scale = np.abs(Vs).max(axis=1)
     np.testing.assert_allclose(err[native.WEAK], 0.01 / scale)
     np.testing.assert_allclose(err[native.WEAK_LEARNED], 1e-4, rtol=1e-9)
+
+
+def test_bench_predictor_study_glue(monkeypatch):
+    """bench.py's predictor study assembles its JSON from the driver's
+    results: run here with stand-ins for the GPU calls (shapes only)."""
+    import json
+    import types
+    torch = pytest.importorskip("torch")
+    import bench
+    from paper_2603_24010_gb300 import native, predictor as PR
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a, **k: None)
+
+    def ens_samples(cfgs, steps=None, capacity=(0, 0, 0)):
+        n = steps - native.PRED_WINDOW
+        return torch.zeros(len(cfgs) * n, native.MLP_IN), torch.zeros(len(cfgs) * n, native.MLP_OUT)
+
+    def samples(cfg, steps=None):
+        n = (steps or cfg["steps"]) - native.PRED_WINDOW
+        return torch.zeros(n, native.MLP_IN), torch.zeros(n, native.MLP_OUT)
+
+    def train(X, Y, iters=1, batch=1, seed=0, **k):
+        return np.zeros(native.MLP_NPARAM, np.float32), native.cp_predictor(), [1.0, 0.1]
+
+    def runs(V, dv):
+        return {native.STRICT: dict(V_gap=V, J_hat=0 * V, ms_per_step=1.0),
+                native.WEAK: dict(V_gap=V + dv, J_hat=0 * V, ms_per_step=1.0),
+                native.WEAK_LEARNED: dict(V_gap=V + dv / 100, J_hat=0 * V + 1, ms_per_step=1.0)}
+
+    def ens_eval(cfgs, params, norm, steps=None, capacity=(0, 0, 0), modes=None):
+        return runs(np.ones((len(cfgs), steps + 1)), 0.01)
+
+    def evaluate(cfg, params, norm, steps=None, modes=None):
+        return runs(np.ones((steps or cfg["steps"]) + 1), 0.01)
+
+    monkeypatch.setattr(PR, "ensemble_strict_samples", ens_samples)
+    monkeypatch.setattr(PR, "strict_samples", samples)
+    monkeypatch.setattr(PR, "train", train)
+    monkeypatch.setattr(PR, "ensemble_evaluate", ens_eval)
+    monkeypatch.setattr(PR, "evaluate", evaluate)
+    args = types.SimpleNamespace(coupling_steps=100, coupling_factor=100, coupling_train=3,
+                                 coupling_train_full=2, coupling_eval=4, coupling_eval_full=2,
+                                 coupling_iters=5)
+    out = json.loads(json.dumps(bench.run_coupling(args)))
+    assert out["samples"] == 5 * (100 - native.PRED_WINDOW)
+    assert out["vgap_err_weak"] == pytest.approx(0.01)
+    assert out["vgap_err_learned"] == pytest.approx(1e-4)
+    assert out["learned_better_frac"] == 1.0
+    assert [r["seed"] for r in out["full_size"]] == [2000, 2001]
