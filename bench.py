@@ -449,6 +449,29 @@ def gap2d_main(args, config):
 
 
 # ---------------------------------------------------------------- coupling
+# Seed ranges of the predictor study.  Training and held-out seeds come from
+# disjoint ranges (a held-out run must be a run the network never saw); the
+# thinned and full-size runs of one seed share the seed-drawn physics (beam
+# mode) but not their particle draws.
+TRAIN_SEED0, TRAIN_FULL_SEED0 = 1000, 500_000
+EVAL_SEED0, EVAL_FULL_SEED0 = 1_000_000, 2_000_000
+
+
+def coupling_seeds(args):
+    """Seeds of the thinned training runs, full-size training runs, thinned
+    held-out runs and full-size held-out runs; raises if any held-out seed is
+    also a training seed."""
+    s = {"train": [TRAIN_SEED0 + k for k in range(args.coupling_train)],
+         "train_full": [TRAIN_FULL_SEED0 + k for k in range(args.coupling_train_full)],
+         "eval": [EVAL_SEED0 + k for k in range(args.coupling_eval)],
+         "eval_full": [EVAL_FULL_SEED0 + k for k in range(args.coupling_eval_full)]}
+    train = set(s["train"]) | set(s["train_full"])
+    held = set(s["eval"]) | set(s["eval_full"])
+    if train & held:
+        raise ValueError("predictor study: held-out seeds overlap the training seeds")
+    return s
+
+
 def run_coupling(args):
     """The learned weak-coupling predictor on the large gap's distribution:
     an ensemble of thinned strict runs plus a few full-size strict runs
@@ -462,11 +485,12 @@ def run_coupling(args):
     S, f = args.coupling_steps, args.coupling_factor
     fam = lambda seed: W.gap_1d_fp32_thinned(seed, factor=f, steps=S)  # noqa: E731
     big = lambda seed: dict(W.gap_1d_fp32_large(seed), steps=S)  # noqa: E731
+    seeds = coupling_seeds(args)
     t0 = time.perf_counter()
-    X, Y = PR.ensemble_strict_samples([fam(1000 + k) for k in range(args.coupling_train)], S)
+    X, Y = PR.ensemble_strict_samples([fam(s) for s in seeds["train"]], S)
     Xf, Yf = [X], [Y]
-    for k in range(args.coupling_train_full):
-        xk, yk = PR.strict_samples(big(3000 + k), S)
+    for s in seeds["train_full"]:
+        xk, yk = PR.strict_samples(big(s), S)
         Xf.append(xk)
         Yf.append(yk)
     X, Y = torch.cat(Xf), torch.cat(Yf)
@@ -480,26 +504,27 @@ def run_coupling(args):
     del X, Y
     torch.cuda.empty_cache()
     t0 = time.perf_counter()
-    res = PR.ensemble_evaluate([fam(2000 + k) for k in range(args.coupling_eval)], params, norm, S)
+    res = PR.ensemble_evaluate([fam(s) for s in seeds["eval"]], params, norm, S)
     errs = PR.ensemble_vgap_errors(res)
     used = (res[native.WEAK_LEARNED]["J_hat"] != 0).mean(axis=1)
     full = []
-    for k in range(args.coupling_eval_full):
-        rk = PR.evaluate(big(2000 + k), params, norm, S)
+    for s in seeds["eval_full"]:
+        rk = PR.evaluate(big(s), params, norm, S)
         ek = PR.vgap_errors(rk)
-        full.append({"seed": 2000 + k, "vgap_err_weak": ek[native.WEAK],
+        full.append({"seed": s, "vgap_err_weak": ek[native.WEAK],
                      "vgap_err_learned": ek[native.WEAK_LEARNED],
                      "predictor_used_frac": float((rk[native.WEAK_LEARNED]["J_hat"] != 0).mean()),
                      "ms_per_step": {"strict": rk[native.STRICT]["ms_per_step"],
                                      "weak": rk[native.WEAK]["ms_per_step"],
                                      "weak_learned": rk[native.WEAK_LEARNED]["ms_per_step"]}})
     t_eval = time.perf_counter() - t0
-    cfg = fam(2000)
+    cfg = fam(seeds["eval"][0] if seeds["eval"] else 0)
     return {
         "workload": ("gap_1d_fp32_thinned: the large gap's distribution (4096 cells, seed-drawn "
                      "beam mode) with %d x fewer, heavier macroparticles: %d pairs, %d beam "
                      "ions/step, dt %.3g s, %d steps; plus full-size runs of the large gap"
                      % (f, cfg["n_pairs"], cfg["beam_per_step"], cfg["dt"], S)),
+        "seeds": {k: ([v[0], v[-1]] if v else []) for k, v in seeds.items()},
         "train_runs": args.coupling_train, "train_runs_full_size": args.coupling_train_full,
         "eval_runs": args.coupling_eval, "eval_runs_full_size": args.coupling_eval_full,
         "data": "thinned training runs generated as one strict ensemble, full-size ones one by "
@@ -574,7 +599,7 @@ def main():
     ap.add_argument("--coupling-eval", type=int, default=256)
     ap.add_argument("--coupling-train-full", type=int, default=16,
                     help="full-size strict training runs added to the thinned ones")
-    ap.add_argument("--coupling-eval-full", type=int, default=2,
+    ap.add_argument("--coupling-eval-full", type=int, default=16,
                     help="full-size held-out seeds evaluated one run per scheme")
     ap.add_argument("--coupling-steps", type=int, default=20000)
     ap.add_argument("--coupling-factor", type=int, default=100)

@@ -93,4 +93,23 @@ def test_bench_predictor_study_glue(monkeypatch):
     assert out["vgap_err_weak"] == pytest.approx(0.01)
     assert out["vgap_err_learned"] == pytest.approx(1e-4)
     assert out["learned_better_frac"] == 1.0
-    assert [r["seed"] for r in out["full_size"]] == [2000, 2001]
+    assert [r["seed"] for r in out["full_size"]] == [bench.EVAL_FULL_SEED0, bench.EVAL_FULL_SEED0 + 1]
+
+
+def test_predictor_study_holds_out_its_evaluation_seeds(monkeypatch):
+    """No held-out seed of the predictor study (thinned or full size) is a
+    training seed, at the default sizes and at the largest the ranges allow;
+    overlapping ranges are refused."""
+    import types
+    import bench
+    for n_train, n_eval in ((2048, 256), (400_000, 900_000)):
+        args = types.SimpleNamespace(coupling_train=n_train, coupling_train_full=16,
+                                     coupling_eval=n_eval, coupling_eval_full=16)
+        s = bench.coupling_seeds(args)
+        assert len(s["train"]) == n_train and len(s["eval"]) == n_eval
+        train = set(s["train"]) | set(s["train_full"])
+        assert not train & (set(s["eval"]) | set(s["eval_full"]))
+    monkeypatch.setattr(bench, "EVAL_SEED0", bench.TRAIN_SEED0 + 10)
+    with pytest.raises(ValueError):
+        bench.coupling_seeds(types.SimpleNamespace(coupling_train=64, coupling_train_full=1,
+                                                   coupling_eval=4, coupling_eval_full=1))
