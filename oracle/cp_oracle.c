@@ -170,6 +170,130 @@ void or_see_electron_batch(const or_params* p, uint64_t id0, int64_t n, int64_t 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Initial plasma: the gap starts filled with a uniform plasma of density n0  */
+/* at temperature T (the paper's runs start from a loaded plasma, Sec. 3.1;  */
+/* the density and temperature are the workload's).  Electrons and ions are  */
+/* loaded in co-located pairs, so the initial charge density is exactly      */
+/* zero.  Pair k: Philox4x64-10 counter (k, 0, 0, 0) under key (seed, load   */
+/* tag); draw 0 places the pair uniformly in the gap, xi = N u0; draws 1 and */
+/* 2 give a Box-Muller pair of standard normals, z_e = r cos(2 pi u2) and    */
+/* z_i = r sin(2 pi u2) with r = sqrt(-2 ln u1), scaled by each species'     */
+/* thermal speed sqrt(e T / m) in cells per step (a Maxwellian in 1D).        */
+/* ------------------------------------------------------------------------ */
+void or_load_pairs(const or_params* p, int64_t n, double T_eV, uint64_t seed, double* xi,
+                   double* u_e, double* u_i) {
+  const double pi = 3.14159265358979323846;
+  const double Nd = (double)p->n_cells;
+  const double dx = p->d / Nd;
+  const double th_e = sqrt(p->e * T_eV / p->m_e) * p->dt / dx;
+  const double th_i = sqrt(p->e * T_eV / p->m_i) * p->dt / dx;
+  for (int64_t k = 0; k < n; ++k) {
+    uint64_t ctr[4] = {(uint64_t)k, 0, 0, 0}, key[2] = {seed, OR_TAG_LOAD}, w[4];
+    or_philox4x64_10(ctr, key, w);
+    double x = Nd * or_u01(w[0]);
+    if (x >= Nd) x = nextafter(Nd, 0.0);
+    const double r = sqrt(-2.0 * log(or_u01(w[1])));
+    const double a = 2.0 * pi * or_u01(w[2]);
+    xi[k] = x;
+    u_e[k] = th_e * (r * cos(a));
+    u_i[k] = th_i * (r * sin(a));
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tesla transformer circuit, Sec. 2.1 and App. A.  Loop equations          */
+/* (Eqs. loop_1-loop_5), with X' the time derivative:                        */
+/*   Q1/C1 + R1 (Q1 - Q2 - Q5)' = 0                                          */
+/*   R1 (-Q1 + Q2 + Q5)' + R2 Q2' + L1 Q2'' + M Q3'' = 0                     */
+/*   M Q2'' + L2 Q3'' + R3 (Q3 - Q4 + Q5)' = 0                               */
+/*   R3 (-Q3 + Q4 - Q5)' + Q4/C3 = 0                                         */
+/*   R1 (-Q1 + Q2 + Q5)' + Q5/C2 + R3 (Q3 - Q4 + Q5)' = 0                    */
+/* BDF2 (App. A): X' = a X^n - (4 X^{n-1} - X^{n-2})/(2 dt), a = 3/(2 dt),    */
+/* X'' = b X^n - (24 X^{n-1} - 22 X^{n-2} + 8 X^{n-3} - X^{n-4})/(4 dt^2),    */
+/* b = 9/(4 dt^2).  The level-n terms form T Q^n, the history terms C        */
+/* (derived here from the loop equations; the printed off-diagonal block and */
+/* right-hand side of App. A disagree with them).  Coupled to the gap, the   */
+/* load capacitor's voltage Q4/C3 is the electrode potential phi_0 (Sec.      */
+/* 2.4.2): row 4 loses its 1/C3 and phi_0 moves to the right-hand side.      */
+/* ------------------------------------------------------------------------ */
+void or_tesla_matrix(const or_params* p, int coupled, double T[25]) {
+  const double a = 3.0 / (2.0 * p->dt), b = 9.0 / (4.0 * p->dt * p->dt);
+  const double r1 = a * p->tR1, r2 = a * p->tR2, r3 = a * p->tR3;
+  const double m = b * p->tM;
+  for (int k = 0; k < 25; ++k) T[k] = 0.0;
+  /* loop 1 */
+  T[0] = 1.0 / p->tC1 + r1; T[1] = -r1; T[4] = -r1;
+  /* loop 2 */
+  T[5] = -r1; T[6] = r1 + r2 + b * p->tL1; T[7] = m; T[9] = r1;
+  /* loop 3 */
+  T[11] = m; T[12] = b * p->tL2 + r3; T[13] = -r3; T[14] = r3;
+  /* loop 4 */
+  T[17] = -r3; T[18] = r3 + (coupled ? 0.0 : 1.0 / p->tC3); T[19] = -r3;
+  /* loop 5 */
+  T[20] = -r1; T[21] = r1; T[22] = r3; T[23] = -r3; T[24] = r1 + r3 + 1.0 / p->tC2;
+}
+
+/* History terms of the BDF2 loop equations: Qh[k] holds the loop charges of
+   level n-1-k. */
+void or_tesla_rhs(const or_params* p, const double Qh[4][5], double c[5]) {
+  const double dt = p->dt;
+  double h1[5], h2[5]; /* first- and second-derivative history of each loop charge */
+  for (int i = 0; i < 5; ++i) {
+    h1[i] = (4.0 * Qh[0][i] - Qh[1][i]) / (2.0 * dt);
+    h2[i] = (24.0 * Qh[0][i] - 22.0 * Qh[1][i] + 8.0 * Qh[2][i] - Qh[3][i]) / (4.0 * dt * dt);
+  }
+  const double x1 = h1[0] - h1[1] - h1[4];  /* of (Q1 - Q2 - Q5), the R1 branch */
+  const double x3 = h1[2] - h1[3] + h1[4];  /* of (Q3 - Q4 + Q5), the R3 branch */
+  c[0] = p->tR1 * x1;
+  c[1] = -p->tR1 * x1 + p->tR2 * h1[1] + p->tL1 * h2[1] + p->tM * h2[2];
+  c[2] = p->tM * h2[1] + p->tL2 * h2[2] + p->tR3 * x3;
+  c[3] = -p->tR3 * x3;
+  c[4] = -p->tR1 * x1 + p->tR3 * x3;
+}
+
+/* Dense 5 x 5 solve, Gaussian elimination with partial pivoting. */
+int or_solve5(const double A[25], const double b[5], double x[5]) {
+  double M[5][6];
+  for (int i = 0; i < 5; ++i) {
+    for (int j = 0; j < 5; ++j) M[i][j] = A[5 * i + j];
+    M[i][5] = b[i];
+  }
+  for (int k = 0; k < 5; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < 5; ++i)
+      if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
+    if (!(fabs(M[piv][k]) > 0.0)) return OR_ERR_ARG;
+    if (piv != k)
+      for (int j = 0; j < 6; ++j) { double tmp = M[k][j]; M[k][j] = M[piv][j]; M[piv][j] = tmp; }
+    for (int i = k + 1; i < 5; ++i) {
+      const double f = M[i][k] / M[k][k];
+      for (int j = k; j < 6; ++j) M[i][j] -= f * M[k][j];
+    }
+  }
+  for (int i = 4; i >= 0; --i) {
+    double s = M[i][5];
+    for (int j = i + 1; j < 5; ++j) s -= M[i][j] * x[j];
+    x[i] = s / M[i][i];
+  }
+  return OR_OK;
+}
+
+static void shift_hist5(double Qh[4][5], const double Qn[5]) {
+  for (int k = 3; k > 0; --k)
+    for (int i = 0; i < 5; ++i) Qh[k][i] = Qh[k - 1][i];
+  for (int i = 0; i < 5; ++i) Qh[0][i] = Qn[i];
+}
+
+int or_tesla_step(const or_params* p, double Qh[4][5]) {
+  double T[25], c[5], Qn[5];
+  or_tesla_matrix(p, 0, T);
+  or_tesla_rhs(p, (const double(*)[5])Qh, c);
+  if (or_solve5(T, c, Qn) != OR_OK) return OR_ERR_ARG;
+  shift_hist5(Qh, Qn);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Coupled field solve at one time level (Sec. 2.4.2-2.4.3, App. A, App. B). */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -184,14 +308,16 @@ static double row_apply(int64_t N, double b0, const double* phi, int64_t i) {
 
 static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_t conv_count,
                       double sigma_prev, const double* Qh, double phi0_prev, double J_hat,
-                      double t, double tol, double* phi, double* E, or_solve_out* o) {
+                      double t, double tol, double* phi, double* E, or_solve_out* o,
+                      const double (*Qt)[5], int step_circuit, double* Qt_new) {
   const int64_t N = p->n_cells;
   const double dx = p->d / (double)N;
   const double A = p->area;
   const double eps0 = p->eps0;
   const double dt = p->dt;
   const double qw = p->e * p->weight;
-  const double scale = qw / (A * dx * FIX); /* rho_i = G_i * scale */
+  const double units = (p->grid_units > 0.0) ? p->grid_units : FIX;
+  const double scale = qw / (A * dx * units); /* rho_i = G_i * scale */
   const double Qconv = (double)conv_count * qw;
   const double Vs = p->polarity * or_source(p, t);
   const double Q1 = Qh[0], Q2 = Qh[1], Q3 = Qh[2], Q4 = Qh[3];
@@ -204,7 +330,30 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
                       p->R * (4.0 * Q1 - Q2) / (2.0 * dt);
   double g = 0.0, Qpart = Q1, gam = 0.0;
   int circuit = (int)p->circuit;
-  if (circuit == OR_CIRCUIT_SERIES_RLC) {
+  /* Tesla transformer: Q1 above is the load capacitor's loop charge Q4^{n-1} */
+  double Tq[25], cq[5], uq[5], wq[5];
+  const int tesla = (circuit == OR_CIRCUIT_TESLA);
+  if (tesla && !Qt) return OR_ERR_ARG;
+  if (tesla && step_circuit) {
+    or_tesla_rhs(p, Qt, cq);
+    if (mode == OR_MODE_STRICT) {
+      /* Sec. 2.4.2: Q4^n = K - [T'^{-1}]_44 phi_0^n (Eqs. Q4_phi_relation, K_def) */
+      const double e4[5] = {0.0, 0.0, 0.0, 1.0, 0.0};
+      or_tesla_matrix(p, 1, Tq);
+      if (or_solve5(Tq, cq, uq) != OR_OK || or_solve5(Tq, e4, wq) != OR_OK) return OR_ERR_ARG;
+      g = wq[3];
+      Qpart = uq[3]; /* K */
+      gam = g * dx / (eps0 * A);
+    } else {
+      /* weak (Sec. 2.4.3): the circuit alone, the load capacitor's voltage
+         starting from phi_0^{n-1}: loop 4 reads
+         R3 (-Q3 + Q4 - Q5)' + phi_0^{n-1} + (Q4 - Q4^{n-1} + J_hat)/C3 = 0 */
+      or_tesla_matrix(p, 0, Tq);
+      cq[3] += -phi0_prev + (Q1 - J_hat) / p->tC3;
+      if (or_solve5(Tq, cq, uq) != OR_OK) return OR_ERR_ARG;
+      Qpart = uq[3];
+    }
+  } else if (circuit == OR_CIRCUIT_SERIES_RLC) {
     if (mode == OR_MODE_STRICT) {
       /* Eqs. Q4_phi_relation, K_def in scalar form: Q^n = K - g phi_0^n. */
       g = 1.0 / (a2 + a1);
@@ -270,6 +419,20 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
       double kden = (a2 + a1) * fabs(Qn) + fabs(Vs + hist) + fabs(phi[0]);
       if (kden > 0.0) eta = fmax(eta, fabs(kvl) / kden);
     }
+    if (tesla && step_circuit && mode == OR_MODE_STRICT) {
+      /* the five loop rows with Q^n = T'^{-1}(c - phi_0 e4) */
+      double Qv[5];
+      for (int i = 0; i < 5; ++i) Qv[i] = uq[i] - phi[0] * wq[i];
+      for (int i = 0; i < 5; ++i) {
+        double lhs = 0.0, den = fabs(cq[i]) + ((i == 3) ? fabs(phi[0]) : 0.0);
+        for (int j = 0; j < 5; ++j) {
+          lhs += Tq[5 * i + j] * Qv[j];
+          den += fabs(Tq[5 * i + j] * Qv[j]);
+        }
+        const double ri = lhs - cq[i] + ((i == 3) ? phi[0] : 0.0);
+        if (den > 0.0) eta = fmax(eta, fabs(ri) / den);
+      }
+    }
     if (!(eta > tol) || sweep == 3) break;
     or_thomas(N, a, b, c, res, dlt);
     for (int64_t i = 0; i < N; ++i) phi[i] -= dlt[i];
@@ -283,7 +446,17 @@ static int solve_core(const or_params* p, int32_t mode, const int64_t* G, int64_
      mode).  Q^n is the circuit's loop charge in both modes; in weak mode the
      capacitor state for the next level is C phi_0^n (Sec. 2.4.3), carried as
      the level's phi_0. */
-  if (circuit == OR_CIRCUIT_SERIES_RLC && mode == OR_MODE_STRICT) {
+  if (tesla) {
+    double Qv[5];
+    for (int i = 0; i < 5; ++i)
+      Qv[i] = !step_circuit ? Qt[0][i]  /* level 0: the state before the first step */
+              : (mode == OR_MODE_STRICT) ? uq[i] - phi[0] * wq[i] : uq[i];
+    if (Qt_new)
+      for (int i = 0; i < 5; ++i) Qt_new[i] = Qv[i];
+    o->Qn = Qv[3];
+    o->sigma_n = sigma_prev + (Qconv + o->Qn - Q1) / A; /* Eq. sigma_update / top_plate_charge */
+    o->I = (3.0 * o->Qn - 4.0 * Q1 + Q2) / (2.0 * dt);
+  } else if (circuit == OR_CIRCUIT_SERIES_RLC && mode == OR_MODE_STRICT) {
     o->Qn = Qpart - g * phi[0];
     o->sigma_n = sigma_prev + (Qconv + o->Qn - Q1) / A;
     o->I = (3.0 * o->Qn - 4.0 * Q1 + Q2) / (2.0 * dt);
@@ -309,7 +482,7 @@ int or_solve_fields(const or_params* p, int32_t mode, const int64_t* G, int64_t 
   or_solve_out o = {0, 0, 0, 0};
   if (mode == OR_MODE_WEAK_LEARNED) mode = OR_MODE_WEAK;
   int rc = solve_core(p, mode, G, conv_count, sigma_prev, Qhist, phi0_prev, J_hat, t, tol, phi,
-                      E, &o);
+                      E, &o, NULL, 1, NULL);
   out[0] = o.Qn;
   out[1] = o.sigma_n;
   out[2] = o.I;
@@ -333,6 +506,7 @@ struct or_state {
   double* E;    /* N edges */
   double sigma; /* sigma_+ of the current level */
   double Qh[4]; /* Q^{n}, Q^{n-1}, Q^{n-2}, Q^{n-3} after the solve at level n */
+  double Qt[4][5]; /* Tesla circuit: loop charges of levels n, n-1, n-2, n-3 */
   int64_t level;
   int solved0, pushed;
   uint64_t beam_id_base;
@@ -379,7 +553,13 @@ or_state* or_create(const or_params* p) {
   s->phi = (double*)calloc((size_t)(s->N + 1), sizeof(double));
   s->E = (double*)calloc((size_t)s->N, sizeof(double));
   s->sigma = p->sigma0;
+  if (p->circuit == OR_CIRCUIT_TESLA) /* C1 charged, no current, before t = 0 */
+    for (int k = 0; k < 4; ++k) s->Qt[k][0] = p->tC1 * p->tV1;
   return s;
+}
+
+void or_tesla_state(const or_state* s, double Q[5]) {
+  for (int i = 0; i < 5; ++i) Q[i] = s->Qt[0][i];
 }
 
 void or_destroy(or_state* s) {
@@ -469,9 +649,11 @@ static int solve_level(or_state* s, int32_t mode, double tol, int64_t conv_count
       s->err_avg <= s->bound * s->J_avg)
     J_used = s->J_pred;
   const int32_t core_mode = (mode == OR_MODE_STRICT) ? OR_MODE_STRICT : OR_MODE_WEAK;
+  double Qt_new[5] = {0, 0, 0, 0, 0};
   int rc = solve_core(&s->p, core_mode, s->G, conv_count, s->sigma, Qhist, phi0_prev, J_used, t,
-                      tol, s->phi, s->E, &o);
-  if (rc == OR_ERR_NONFINITE) return rc;
+                      tol, s->phi, s->E, &o, (const double(*)[5])s->Qt, s->solved0, Qt_new);
+  if (rc == OR_ERR_NONFINITE || rc == OR_ERR_ARG) return rc;
+  if (s->p.circuit == OR_CIRCUIT_TESLA && s->solved0) shift_hist5(s->Qt, Qt_new);
   if (s->has_pred) {
     /* the prediction for this level against the realised J */
     if (s->pred_ready) {
@@ -516,7 +698,7 @@ static int solve_level(or_state* s, int32_t mode, double tol, int64_t conv_count
   d->conv_count = conv_count;
   d->Q_conv = (double)conv_count * s->p.e * s->p.weight;
   d->Q_circ = o.Qn;
-  d->V_source = s->p.polarity * or_source(&s->p, t);
+  d->V_source = (s->p.circuit == OR_CIRCUIT_TESLA) ? 0.0 : s->p.polarity * or_source(&s->p, t);
   d->residual = o.resid;
   for (int sp = 0; sp < OR_SPECIES; ++sp) d->n_live[sp] = s->n[sp];
   int prc = push_diag(s, d);
@@ -685,7 +867,8 @@ int or_get_particles(const or_state* s, int32_t sp, double* xi, double* u, uint3
 }
 
 int or_read_grid(const or_state* s, double* phi, double* rho, double* E, int64_t* G) {
-  const double scale = s->p.e * s->p.weight / (s->p.area * s->dx * FIX);
+  const double units = (s->p.grid_units > 0.0) ? s->p.grid_units : FIX;
+  const double scale = s->p.e * s->p.weight / (s->p.area * s->dx * units);
   for (int64_t i = 0; i <= s->N; ++i) {
     if (phi) phi[i] = s->phi[i];
     if (rho) rho[i] = (double)s->G[i] * scale;

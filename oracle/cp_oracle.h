@@ -32,6 +32,7 @@
 
 #define OR_CIRCUIT_SERIES_RLC 0 /* series R-L-source into the gap */
 #define OR_CIRCUIT_OPEN 1       /* floating electrode: no circuit charge */
+#define OR_CIRCUIT_TESLA 2      /* the paper's 5-loop Tesla transformer (Eqs. loop_1-loop_5) */
 
 #define OR_OK 0
 #define OR_ERR_ARG (-1)
@@ -41,6 +42,7 @@
 /* Philox stream tags (second key word). */
 #define OR_TAG_SEE 0x5345ULL
 #define OR_TAG_BEAM 0x4245ULL
+#define OR_TAG_LOAD 0x4C4F4144ULL
 
 typedef struct {
   /* gap, Sec. 2.2.1 and App. B */
@@ -66,6 +68,12 @@ typedef struct {
   double dt;       /* time step [s] */
   double weight;   /* macroparticle weight (physical particles per macroparticle) */
   double sigma0;   /* initial surface charge density sigma_+^{-1} [C/m^2] */
+  double grid_units; /* charge-grid units per macroparticle charge (0: 2^16, the 1D
+                        deposit's; the 2D gap's transverse mean is in 2^32) */
+  /* Tesla transformer (circuit == OR_CIRCUIT_TESLA, Sec. 2.1): loop charges
+     Q1..Q5 of Eqs. loop_1-loop_5; the gap is the load capacitor C3 (its
+     charge is Q4), C1 is pre-charged to V1 at t = 0 */
+  double tR1, tR2, tR3, tC1, tC2, tC3, tL1, tL2, tM, tV1;
   uint64_t seed;
   int64_t n_cells;       /* N: nodes 0..N, phi_N = 0 */
   int64_t circuit;       /* OR_CIRCUIT_* */
@@ -113,6 +121,21 @@ void or_see_count_batch(const or_params* p, double E_ion_eV, uint64_t id0, int64
                         int64_t step, int64_t* counts);
 void or_see_electron_batch(const or_params* p, uint64_t id0, int64_t n, int64_t step,
                            double* v, double* frac);
+
+/* Tesla transformer pieces (or_tesla_* in cp_oracle.c). */
+void or_tesla_matrix(const or_params* p, int coupled, double T[25]);
+void or_tesla_rhs(const or_params* p, const double Qh[4][5], double c[5]);
+int or_solve5(const double A[25], const double b[5], double x[5]);
+/* One BDF2 step of the circuit alone (C3 an ordinary capacitor): Qh holds
+   the loop charges of the last four levels (Qh[0] newest) and is shifted. */
+int or_tesla_step(const or_params* p, double Qh[4][5]);
+/* Loop charges Q1..Q5 of the current level of a Tesla gap. */
+void or_tesla_state(const or_state* s, double Q[5]);
+
+/* Initial plasma of n co-located electron/ion pairs at temperature T_eV
+   (cell units, see or_load_pairs in cp_oracle.c). */
+void or_load_pairs(const or_params* p, int64_t n, double T_eV, uint64_t seed, double* xi,
+                   double* u_e, double* u_i);
 
 /* ---- whole-gap state ---- */
 or_state* or_create(const or_params* p);

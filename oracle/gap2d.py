@@ -10,8 +10,10 @@ mean.  Each step follows the 1D order (push, absorption + SEE, beam,
 deposit, solve) with:
 
 * deposit: bilinear cloud-in-cell to nodes with per-axis fixed-point
-  weights floor(frac 2^8) (corner products sum to 2^16 per macroparticle),
-  end nodes in x doubled as in App. E.2;
+  weights floor(frac 2^16) (corner products sum to 2^32 per macroparticle),
+  end nodes in x doubled as in App. E.2 -- plain CIC with positions snapped
+  to 2^-16 of a cell per axis, which moves the fields by far less than the
+  1e-5 tolerance (tests/test_oracle_deposit_resolution.py);
 * solve: the transverse mean of the charge (the integer column sums of the
   grid) is the 1D coupled problem of Sec. 2.4.2/2.4.3 with the circuit row,
   solved by the 1D oracle; the rest is expanded in transverse Fourier modes
@@ -34,7 +36,8 @@ import numpy as np
 
 from . import oracle as O
 
-FIX_AXIS = 256  # 2^8 per axis, 2^16 per macroparticle
+FIX_AXIS = 65536  # 2^16 per axis, 2^32 per macroparticle
+GRID_UNITS = FIX_AXIS * FIX_AXIS
 
 
 def deposit2d(Nx, Ny, xi, eta, sign, G=None):
@@ -89,8 +92,9 @@ def gather2d(Ex, Ey, xi, eta):
 
 
 def cfg_1d(cfg):
-    """The 1D problem of the transverse mean (same gap, circuit and weight)."""
-    return dict(cfg)
+    """The 1D problem of the transverse mean (same gap, circuit and weight;
+    its charge grid, the column sums, counts 2^32 per macroparticle)."""
+    return dict(cfg, grid_units=float(GRID_UNITS))
 
 
 def solve2d(cfg, mode, G, conv_count, sigma_prev, Qhist, t, phi0_prev, tol=1e-12):
@@ -105,7 +109,7 @@ def solve2d(cfg, mode, G, conv_count, sigma_prev, Qhist, t, phi0_prev, tol=1e-12
     rc, phi0, _, out = O.solve_fields(cfg_1d(cfg), mode, G1, conv_count, sigma_prev, Qhist, t,
                                       tol=tol, phi0_prev=phi0_prev)
     # the other transverse modes, phi = 0 on both electrodes
-    scale = cfg["e"] * cfg["weight"] / (dx * dy * Lz * 65536.0)
+    scale = cfg["e"] * cfg["weight"] / (dx * dy * Lz * float(GRID_UNITS))
     rho = G.astype(np.float64) * scale
     rho_t = rho - rho.mean(axis=1, keepdims=True)
     R = np.fft.fft(rho_t, axis=1)

@@ -13,7 +13,7 @@ from . import build_oracle
 ELECTRONS, IONS, SECONDARIES = 0, 1, 2
 STRICT, WEAK, WEAK_LEARNED = 0, 1, 2
 MLP_IN, MLP_OUT, MLP_NPARAM = 40, 2, 11074
-SERIES_RLC, OPEN = 0, 1
+SERIES_RLC, OPEN, TESLA = 0, 1, 2
 OK, ERR_ARG, ERR_RESIDUAL, ERR_NONFINITE = 0, -1, -5, -6
 TAG_SEE, TAG_BEAM = 0x5345, 0x4245
 
@@ -22,7 +22,8 @@ class OrParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "d", "area", "eps0", "e", "m_e", "m_i", "R", "L", "C", "V0", "f", "tau",
         "polarity", "gamma_coef", "gamma_max", "E_ref_eV", "see_scale", "T_emit_eV",
-        "beam_E_eV", "beam_Emin_eV", "beam_Emax_eV", "dt", "weight", "sigma0")] + [
+        "beam_E_eV", "beam_Emin_eV", "beam_Emax_eV", "dt", "weight", "sigma0", "grid_units",
+        "tR1", "tR2", "tR3", "tC1", "tC2", "tC3", "tL1", "tL2", "tM", "tV1")] + [
         ("seed", C.c_uint64), ("n_cells", C.c_int64), ("circuit", C.c_int64),
         ("beam_per_step", C.c_int64), ("beam_mode", C.c_int64)]
 
@@ -64,6 +65,8 @@ def lib():
                                          C.c_int64, ip]
         L.or_see_electron_batch.argtypes = [C.POINTER(OrParams), C.c_uint64, C.c_int64, C.c_int64,
                                             dp, dp]
+        L.or_load_pairs.argtypes = [C.POINTER(OrParams), C.c_int64, C.c_double, C.c_uint64, dp, dp,
+                                    dp]
         L.or_create.argtypes = [C.POINTER(OrParams)]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
@@ -178,6 +181,15 @@ def see_electron_batch(cfg, id0, n, step):
     fr = np.zeros(int(n))
     lib().or_see_electron_batch(C.byref(p), int(id0), int(n), int(step), _dp(v), _dp(fr))
     return v, fr
+
+
+def load_pairs(cfg, n, T_eV, seed):
+    """The initial plasma of n co-located pairs: (xi, u_e, u_i) in cell units."""
+    p = make_params(cfg)
+    xi, ue, ui = np.zeros(int(n)), np.zeros(int(n)), np.zeros(int(n))
+    lib().or_load_pairs(C.byref(p), int(n), float(T_eV), int(seed) & (2**64 - 1), _dp(xi), _dp(ue),
+                        _dp(ui))
+    return xi, ue, ui
 
 
 def solve_fields(cfg, mode, G, conv_count, sigma_prev, Qhist, t, tol=1e-12, phi0_prev=0.0,

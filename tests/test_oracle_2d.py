@@ -40,16 +40,17 @@ def test_deposit_matches_exact_rationals(g2):
     for x, y in zip(xi, eta):
         fx, fy = Fraction(x), Fraction(y)
         i, j = int(fx // 1), int(fy // 1)
-        wx1 = int((fx - i) * 256 // 1)
-        wy1 = int((fy - j) * 256 // 1)
-        for ii, jj, w in ((i, j, (256 - wx1) * (256 - wy1)), (i + 1, j, wx1 * (256 - wy1)),
-                          (i, (j + 1) % Ny, (256 - wx1) * wy1), (i + 1, (j + 1) % Ny, wx1 * wy1)):
+        F = 65536  # 2^16 per axis
+        wx1 = int((fx - i) * F // 1)
+        wy1 = int((fy - j) * F // 1)
+        for ii, jj, w in ((i, j, (F - wx1) * (F - wy1)), (i + 1, j, wx1 * (F - wy1)),
+                          (i, (j + 1) % Ny, (F - wx1) * wy1), (i + 1, (j + 1) % Ny, wx1 * wy1)):
             want[ii, jj] += w * (2 if ii in (0, Nx) else 1)
     np.testing.assert_array_equal(G, want.astype(np.int64))
     half = G.copy()
     half[0] //= 2
     half[Nx] //= 2
-    assert half.sum() == 65536 * xi.size
+    assert half.sum() == 2**32 * xi.size
 
 
 @pytest.mark.parametrize("Nx,Ny", [(6, 4), (9, 8)])
@@ -64,7 +65,7 @@ def test_fft_solve_equals_dense_2d_system(g2, Nx, Ny):
     assert rc == 0
     dx, dy = cfg["d"] / Nx, cfg["Ly"] / Ny
     Lz = cfg["area"] / cfg["Ly"]
-    rho = G * cfg["e"] * cfg["weight"] / (dx * dy * Lz * 65536.0)
+    rho = G * cfg["e"] * cfg["weight"] / (dx * dy * Lz * 2.0**32)
     eps0 = cfg["eps0"]
     # unknowns: V (electrode) then phi[i, j] for i = 1..Nx-1
     idx = lambda i, j: 1 + (i - 1) * Ny + (j % Ny)  # noqa: E731
@@ -137,7 +138,7 @@ def test_coupled_run_conserves_charge_and_particles(g2, orc):
     G = o.G.copy()
     G[0] //= 2
     G[-1] //= 2
-    assert G.sum() == 65536 * (nl[-1, 1] - nl[-1, 0] - nl[-1, 2])
+    assert G.sum() == 2**32 * (nl[-1, 1] - nl[-1, 0] - nl[-1, 2])
     ab = h["absorbed"]
     np.testing.assert_array_equal(np.diff(nl[:, 1]), -ab[1:, :, 1].sum(axis=1) + 6)
     np.testing.assert_array_equal(np.diff(nl[:, 2]), -ab[1:, :, 2].sum(axis=1) + h["emitted"][1:].sum(axis=1))
