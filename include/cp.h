@@ -160,6 +160,34 @@ int cp_create(const cp_gap* gap, const cp_circuit* circuit, const cp_see_beam* s
 int cp_set_particles(cp_ctx* ctx, int32_t species, const double* x, const double* v,
                      const uint32_t* id, int64_t n, int32_t units);
 
+/* Initial plasma (the paper's runs start from a gap filled with a uniform
+   plasma, Sec. 3.1; density and temperature are the workload's).  n_pairs
+   co-located electron/ion pairs, so the initial charge density is exactly
+   zero: pair k is drawn from Philox4x64-10 counter (k, 0, 0, 0) under key
+   (seed, load tag 0x4C4F4144); draw 0 places it uniformly in the gap
+   (xi = N u0, rounded to the store's precision, kept inside (0, N)) and the
+   Box-Muller pair of draws 1 and 2, z_e = r cos(2 pi u2), z_i = r sin(2 pi
+   u2) with r = sqrt(-2 ln u1), gives the velocities z sqrt(e T_load / m)
+   (a Maxwellian of temperature T_load in 1D, per species).  Ion k gets id k.
+   Weight: `weight` if > 0, else n0 d A / n_pairs if n0 > 0, else the gap's
+   weight is kept; a new weight replaces cp_gap.weight for every species and
+   the beam. */
+typedef struct {
+  double n0;        /* plasma density [m^-3] (0: keep the weight) */
+  double T_load_eV; /* temperature of both species [eV] */
+  int64_t n_pairs;  /* electron/ion pairs (0 <= n_pairs < 2^32) */
+  double weight;    /* physical particles per macroparticle (0: from n0) */
+} cp_species;
+
+/* Draw the initial plasma on the device (no host particle arrays, nothing
+   copied from the host).  Replaces any electrons and ions staged by
+   cp_set_particles; call before the first step (the draw runs when the first
+   step call allocates the stores).  Afterwards cp_set_particles accepts only
+   the secondaries.  Errors: CP_ERR_ARG (after the first step, n_pairs out of
+   range, negative or non-finite T_load_eV, n0 or weight), CP_ERR_CAPACITY
+   (n_pairs above a requested electron or ion capacity). */
+int cp_load_species(cp_ctx* ctx, const cp_species* species, uint64_t seed);
+
 /* Advance n_steps steps with strict (monolithic) coupling, Sec. 2.4.2: the
    circuit's Schur row Q^n = K - g phi_0^n is folded into the x = 0 Poisson row
    (Eq. Poisson_BC2) and the coupled system is solved directly, then refined
@@ -247,13 +275,15 @@ int cp_read_launch_times(cp_ctx* ctx, double* ms, int64_t cap, int64_t* n);
    (seed, step, id[k]), and the deposit of the surviving ions and the
    emitted electrons into G (device, N+1 int64, overwritten; 2^16 per
    macroparticle).  Emitted electrons are written to se_xi/se_u (device,
-   capacity se_cap).  counts (device, 6 int64): ions absorbed at x = 0 and
-   x = d, electrons emitted at x = 0 and x = d, electrons written, and the
-   convection count at x = 0.  The first call on a device looks up the
+   capacity se_cap).  counts (device, 6 int64, written on the device): ions
+   absorbed at x = 0 and x = d, electrons emitted at x = 0 and x = d,
+   electrons written (at most se_cap), and the convection count at x = 0.  The first call on a device looks up the
    scratch array's address; make that first call before any stream capture.
    The call synchronises `stream`.  Every call shares the one scratch array:
    calls that overlap on the GPU (other streams, other host threads) race.
-   Errors: CP_ERR_ARG (null buffer, n_cells outside 2..4096, bad sizes),
+   Errors: CP_ERR_ARG (null buffer, n_cells outside 2..4096, bad sizes, a
+   SEE law cp_create would refuse: gamma_max outside 0..14, a negative or
+   non-finite scale, gamma_coef, E_ref_eV or T_emit_eV),
    CP_ERR_CAPACITY (n > 524288 ions, the scratch's limit; or more emitted
    electrons than se_cap), CP_ERR_CUDA. */
 int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, double dt, uint64_t seed,
@@ -452,8 +482,9 @@ void cp_batch_destroy(cp_batch* b);
  * absorption and SEE at the electrodes (yield from the impact's kinetic
  * energy; emitted electrons start at the impact's y, normal to the wall),
  * beam ions entering at x = d with a Gaussian transverse profile
- * (beam_sigma, centre beam_y0), bilinear fixed-point deposit (2^8 x 2^8 per
- * macroparticle, end nodes in x doubled), and the solve: the transverse mean
+ * (beam_sigma, centre beam_y0), bilinear fixed-point deposit (2^16 x 2^16
+ * per macroparticle, positions resolved to 2^-16 of a cell per axis, end
+ * nodes in x doubled), and the solve: the transverse mean
  * is the 1D coupled problem (strict or weak, with the circuit, exactly as
  * cp_step_strict / cp_step_weak) and the other transverse Fourier modes
  * solve tridiagonal systems in x with phi = 0 on both electrodes.  The
@@ -496,7 +527,9 @@ int cp2d_read_history(cp_gap2d* g, int64_t first, int64_t n, cp_diag* out);
 int cp2d_get_level(cp_gap2d* g, int64_t* level);
 /* Current fields, row-major over x: phi[(Nx+1) Ny], Ex[Nx Ny] at (i+1/2, j),
    Ey[(Nx+1) Ny] at (i, j+1/2), and the charge grid G[(Nx+1) Ny] of the
-   level (2^16 per macroparticle).  Any pointer may be NULL. */
+   level (2^32 per macroparticle).  Any pointer may be NULL.  The stores
+   together hold at most 2^30 macroparticles (the int64 charge sums' range);
+   cp2d_step_* refuse larger capacities with CP_ERR_ARG. */
 int cp2d_read_fields(cp_gap2d* g, double* phi, float* Ex, float* Ey, int64_t* G);
 /* Live particles of one species (cell units); *n receives the count.
    Errors: CP_ERR_CAPACITY if cap is too small. */

@@ -30,6 +30,8 @@ cudaError_t solve_launch(int precision, const Bufs& B, int ctas, size_t smem, cu
                          int do_push, int mode, double tol);
 cudaError_t compact_launch(int precision, const Bufs& B, int grid, cudaStream_t st);
 cudaError_t fill_launch(int precision, void* p, int64_t n, double v, cudaStream_t st);
+cudaError_t load_pairs_launch(int precision, void* xe, void* ue, void* xo, void* uo, uint32_t* id,
+                              int64_t n, int N, double th_e, double th_i, uint64_t seed, cudaStream_t st);
 cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st);
 cudaError_t pack_predictor_launch(const float* params, PredNet* net, cudaStream_t st);
 size_t push_ens_smem_bytes(int n_max, int precision, int E);
@@ -96,6 +98,10 @@ struct cp_ctx {
   // particles staged on the host until the first step
   std::vector<double> hx[kSpecies], hu[kSpecies];
   std::vector<uint32_t> hid;
+  // initial plasma drawn on the device at the first step (cp_load_species)
+  int64_t load_n = -1;  // pairs, or -1 when electrons and ions come from cp_set_particles
+  double load_T = 0.0;
+  uint64_t load_seed = 0;
   cpk::PredNet* net = nullptr;  // installed predictor network (device), or null
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // strict, weak, learned weak
   double gtol[3] = {0.0, 0.0, 0.0};
@@ -119,6 +125,13 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CP_OK : CP_ERR_CUDA; }
 #define CP_CUDA(expr) CP_TRY(cuda_rc(expr))
 
 int64_t round4(int64_t n) { return (n + 3) & ~int64_t(3); }
+
+// macroparticle weight and the charge scales that follow from it
+void set_weight(cpk::DevParams* P, double w) {
+  P->weight = w;
+  P->scale = P->e * P->weight / (P->area * P->dx * cpk::kFix);
+  P->alpha = P->dx * P->dx * P->scale / P->eps0;
+}
 
 cpk::Bufs make_bufs(const cp_ctx* c) {
   cpk::Bufs B;
@@ -178,6 +191,7 @@ int initialize(cp_ctx* c, int mode, double tol) {
   const cpk::DevParams& P = c->hp;
   int64_t n[kSpecies];
   for (int s = 0; s < kSpecies; ++s) n[s] = static_cast<int64_t>(c->hx[s].size());
+  if (c->load_n >= 0) n[CP_ELECTRONS] = n[CP_IONS] = c->load_n;
   const int64_t B = P.beam_per_step;
   const int64_t K = c->compact_every;
   const int64_t ions_ever = n[1] + B * c->max_steps;
@@ -197,9 +211,17 @@ int initialize(cp_ctx* c, int mode, double tol) {
     }
     CP_TRY(alloc(reinterpret_cast<void**>(&c->buf_id[b]), sizeof(uint32_t) * c->cap[1]));
   }
-  // upload in store precision
+  // initial plasma drawn on the device, or upload in store precision
+  if (c->load_n > 0) {
+    const double dxl = P.dx, dtl = P.dt;
+    const double th_e = std::sqrt(P.e * c->load_T / P.m_e) * dtl / dxl;
+    const double th_i = std::sqrt(P.e * c->load_T / P.m_i) * dtl / dxl;
+    CP_CUDA(cpk::load_pairs_launch(c->precision, c->buf_xi[0][CP_ELECTRONS], c->buf_u[0][CP_ELECTRONS],
+                                   c->buf_xi[0][CP_IONS], c->buf_u[0][CP_IONS], c->buf_id[0], c->load_n,
+                                   c->N, th_e, th_i, c->load_seed, c->stream));
+  }
   for (int s = 0; s < kSpecies; ++s) {
-    if (!n[s]) continue;
+    if (!n[s] || (c->load_n >= 0 && s != CP_SECONDARIES)) continue;
     if (c->precision == CP_FP32) {
       std::vector<float> fx(n[s]), fu(n[s]);
       for (int64_t k = 0; k < n[s]; ++k) {
@@ -216,7 +238,9 @@ int initialize(cp_ctx* c, int mode, double tol) {
     }
   }
   uint32_t id_base = 0;
-  if (n[1]) {
+  if (c->load_n >= 0) {
+    id_base = static_cast<uint32_t>(c->load_n);  // ids 0..n_pairs-1
+  } else if (n[1]) {
     CP_CUDA(cudaMemcpyAsync(c->buf_id[0], c->hid.data(), 4 * n[1], cudaMemcpyHostToDevice, c->stream));
     for (uint32_t v : c->hid) id_base = std::max<uint32_t>(id_base, v + 1u);
   }
@@ -478,6 +502,8 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.beam_E_eV = see->beam_E_eV;
   P.beam_Emin_eV = see->beam_Emin_eV;
   P.beam_Emax_eV = see->beam_Emax_eV;
+  // the oracle's order of operations: (sqrt((2 E) e / m_i) dt) / dx, each rounded
+  P.beam_ub = std::sqrt(2.0 * P.beam_E_eV * gap->e / gap->m_i) * run->dt / (gap->d / gap->n_cells);
   P.seed = run->seed;
   P.scale = P.e * P.weight / (P.area * P.dx * cpk::kFix);
   const double dt = P.dt, dx = P.dx;
@@ -512,7 +538,8 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
 int cp_set_particles(cp_ctx* c, int32_t species, const double* x, const double* v,
                      const uint32_t* id, int64_t n, int32_t units) {
   if (!c || species < 0 || species >= kSpecies || n < 0 || c->initialized ||
-      (units != CP_UNITS_CELL && units != CP_UNITS_SI) || (n > 0 && (!x || !v)))
+      (units != CP_UNITS_CELL && units != CP_UNITS_SI) || (n > 0 && (!x || !v)) ||
+      (c->load_n >= 0 && species != CP_SECONDARIES))
     return CP_ERR_ARG;
   if (c->cap_req[species] > 0 && n > c->cap_req[species]) return CP_ERR_CAPACITY;
   const double dx = c->hp.dx, dt = c->hp.dt;
@@ -541,6 +568,29 @@ int cp_set_particles(cp_ctx* c, int32_t species, const double* x, const double* 
   return CP_OK;
 }
 
+int cp_load_species(cp_ctx* c, const cp_species* sp, uint64_t seed) {
+  if (!c || !sp || c->initialized || sp->n_pairs < 0 || sp->n_pairs > 4294967295LL ||
+      !(sp->T_load_eV >= 0.0) || !std::isfinite(sp->T_load_eV) || !(sp->n0 >= 0.0) ||
+      !std::isfinite(sp->n0) || !(sp->weight >= 0.0) || !std::isfinite(sp->weight))
+    return CP_ERR_ARG;
+  for (int s = 0; s < 2; ++s)
+    if (c->cap_req[s] > 0 && sp->n_pairs > c->cap_req[s]) return CP_ERR_CAPACITY;
+  double w = 0.0;
+  if (sp->weight > 0.0) w = sp->weight;
+  else if (sp->n0 > 0.0 && sp->n_pairs > 0)
+    w = sp->n0 * c->hp.d * c->hp.area / static_cast<double>(sp->n_pairs);
+  if (w > 0.0) set_weight(&c->hp, w);
+  for (int s = 0; s < 2; ++s) {
+    std::vector<double>().swap(c->hx[s]);
+    std::vector<double>().swap(c->hu[s]);
+  }
+  std::vector<uint32_t>().swap(c->hid);
+  c->load_n = sp->n_pairs;
+  c->load_T = sp->T_load_eV;
+  c->load_seed = seed;
+  return CP_OK;
+}
+
 int cp_step_strict(cp_ctx* c, int32_t n_steps, double residual_tol) {
   return do_steps(c, 0, n_steps, residual_tol);
 }
@@ -562,7 +612,7 @@ int cp_set_predictor(cp_ctx* c, const float* params, const cp_predictor* norm) {
   for (int k = 0; k < CP_MLP_NPARAM; ++k)
     if (!std::isfinite(params[k])) return CP_ERR_ARG;
   CP_CUDA(cudaSetDevice(c->device));
-  if (!c->net) CP_TRY(alloc(reinterpret_cast<void**>(&c->net), sizeof(cpk::PredNet)));
+  if (!c->net) CP_TRY(alloc(reinterpret_cast<void**>(&c->net), cpk::kPredNetBytes));
   float* dparams = nullptr;
   CP_TRY(alloc(reinterpret_cast<void**>(&dparams), sizeof(float) * CP_MLP_NPARAM));
   int rc = cuda_rc(cudaMemcpyAsync(dparams, params, sizeof(float) * CP_MLP_NPARAM,
@@ -1457,6 +1507,12 @@ int g2_init(cp_gap2d* g, int mode, double tol) {
   c->solve_smem = cpk::solve_smem_bytes(N, c->solve_ctas);
   CP_CUDA(cpk::solve_configure(c->precision, c->solve_smem));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->abs), sizeof(cpk::AbsRec)));
+  // the mean's charge grid (column sums of the 2D grid) counts 2^32 per
+  // macroparticle; every int64 sum stays below 2^63 while the stores hold
+  // fewer than 2^30 macroparticles (a node gets at most twice 2^32 each)
+  if (c->cap[0] + c->cap[1] + c->cap[2] > (int64_t(1) << 30)) return CP_ERR_ARG;
+  P.scale = P.e * P.weight / (P.area * P.dx * cpk::kFix2);
+  P.alpha = P.dx * P.dx * P.scale / P.eps0;
   CP_TRY(alloc(reinterpret_cast<void**>(&c->dP), sizeof(cpk::DevParams)));
   CP_CUDA(cudaMemcpyAsync(c->dP, &c->hp, sizeof(cpk::DevParams), cudaMemcpyHostToDevice, c->stream));
   CP_TRY(alloc(reinterpret_cast<void**>(&c->vs), sizeof(double) * (c->hist_rows + 1)));
@@ -1515,7 +1571,7 @@ int g2_init(cp_gap2d* g, int mode, double tol) {
   D.inv_dx = static_cast<float>(1.0 / D.dx);
   D.inv_dy = static_cast<float>(1.0 / D.dy);
   const double Lz = P.area / g->ly;
-  D.rho_scale = P.e * P.weight / (D.dx * D.dy * Lz * cpk::kFix);
+  D.rho_scale = P.e * P.weight / (D.dx * D.dy * Lz * cpk::kFix2);
   const double dt = P.dt;
   const double q_m[kSpecies] = {-P.e / P.m_e, P.e / P.m_i, -P.e / P.m_e};
   for (int s = 0; s < kSpecies; ++s) {

@@ -319,7 +319,7 @@ k_push_ens(const Bufs* __restrict__ Ball, int E, int n_max, AbsRecE* __restrict_
       const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
       const double vse = Pi->see_vth * fabs(z);
       const double use = vse * dt / dx;
-      const double xd = (el == 0) ? use * frac : static_cast<double>(Ni) - use * frac;
+      const double xd = (el == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(Ni), __dmul_rn(use, frac));
       const real xr = nudge_inside<real>(xd, Ni);
       const real ur = static_cast<real>(el == 0 ? use : -use);
       const unsigned long long slot = wb + static_cast<unsigned long long>(jn);
@@ -362,10 +362,10 @@ k_push_ens(const Bufs* __restrict__ Ball, int E, int n_max, AbsRecE* __restrict_
         const double frac = u01(wv.w[0]);
         const double Eb = (Pi->beam_mode == 0)
                               ? Pi->beam_E_eV
-                              : Pi->beam_Emin_eV + (Pi->beam_Emax_eV - Pi->beam_Emin_eV) * u01(wv.w[1]);
+                              : __dadd_rn(Pi->beam_Emin_eV, __dmul_rn(__dsub_rn(Pi->beam_Emax_eV, Pi->beam_Emin_eV), u01(wv.w[1])));
         const double v = sqrt(2.0 * Eb * Pi->e / Pi->m_i);
         const double ub = v * dt / dx;
-        const real xr = nudge_inside<real>(static_cast<double>(Ni) - ub * frac, Ni);
+        const real xr = nudge_inside<real>(__dsub_rn(static_cast<double>(Ni), __dmul_rn(ub, frac)), Ni);
         const unsigned long long slot =
             wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));
         if (slot < static_cast<unsigned long long>(Pi->cap[CP_IONS])) {

@@ -41,6 +41,7 @@ constexpr double kFix = 65536.0;       // fixed-point units per macroparticle ch
 constexpr uint64_t kTagSee = 0x5345ULL;
 constexpr uint64_t kTagBeam = 0x4245ULL;
 constexpr uint64_t kTagInit = 0x4D4C50ULL;  // MLP parameter initialisation draws
+constexpr uint64_t kTagLoad = 0x4C4F4144ULL;  // initial plasma load
 // predictor network shape and feature window
 constexpr int kPredWindow = 8;
 constexpr int kPredFeat = 5;
@@ -59,6 +60,7 @@ struct DevParams {
   double R, L, C, V0, f, tau, polarity;
   double gamma_coef, gamma_max, E_ref_eV, see_scale, T_emit_eV;
   double beam_E_eV, beam_Emin_eV, beam_Emax_eV;
+  double beam_ub;        // mono-energetic beam speed sqrt(2 E e / m_i) dt / dx [cells/step]
   uint64_t seed;
   double scale;          // rho_i = G_i * scale  [C/m^3]
   double kappa[kSpecies];  // q dt^2 / (m dx): cells/step^2 per V/m
@@ -113,8 +115,9 @@ struct DevState {
   double nxt_Vs, nxt_hist;     // source and BDF2 history of the next level
   double phi0_last;           // phi_0 of the current level (weak: capacitor state)
   // learned weak-coupling predictor (evaluated when a network is installed)
-  double feat[kPredWindow][kPredFeat];  // raw feature rows of the last 8 levels
+  double feat[kPredWindow][kPredFeat];  // raw feature rows of the last 8 levels (a ring)
   int32_t n_feat;             // rows filled (saturates at kPredWindow)
+  int32_t feat_pos;           // ring slot the next level's row goes to
   int32_t pred_ready;         // J_pred holds a prediction for the next level
   double J_pred;              // network's J_hat for the next level [C]
   double err_avg, J_avg;      // running averages of |J - J_hat| and |J|
@@ -137,6 +140,8 @@ struct PredNet {
   float out_scale[kPredOut];
   double bound;
 };
+// bytes of a PredNet as allocated and copied (whole 16-byte chunks)
+constexpr size_t kPredNetBytes = (sizeof(PredNet) + 15) & ~size_t(15);
 
 struct Bufs {
   const DevParams* P;

@@ -10,7 +10,8 @@
 // * k2_push: a persistent grid takes work items of up to 32768 particles of
 //   one tile; the item's field window (the tile plus 4 cells of halo, E_x
 //   and E_y) is staged in shared memory and its charge is deposited into a
-//   shared 32-bit window flushed once per item into the int64 grid.
+//   pair of shared 32-bit windows (a corner weight w < 2^32 + 1 goes in as
+//   w >> 16 and w & 0xffff) flushed once per item into the int64 grid.
 //   Particles that left their window since the sort (and the unsorted tail
 //   of emitted electrons and beam ions) gather from and deposit into global
 //   memory directly, with the same arithmetic.
@@ -104,20 +105,30 @@ __device__ __forceinline__ int win_index(int gx, int gy, int ox, int oy, int Ny)
   return lx * kW2 + ly;
 }
 
-// fixed-point bilinear weights floor(frac 2^8) per axis
+// fixed-point bilinear weights floor(frac 2^16) per axis: the corner
+// products sum to 2^32 per macroparticle (x - floor(x) and the power-of-two
+// scaling are exact, so the truncation decides alone)
 __device__ __forceinline__ void deposit_weights(float x, float y, int Ny, int* i, int* j, int* j1,
-                                                int* w00, int* w10, int* w01, int* w11) {
+                                                unsigned long long* w00, unsigned long long* w10,
+                                                unsigned long long* w01, unsigned long long* w11) {
   const float xf = floorf(x), yf = floorf(y);
   *i = static_cast<int>(xf);
   *j = static_cast<int>(yf);
   *j1 = wrapi(*j + 1, Ny);
-  const int wx1 = static_cast<int>(__float2uint_rz((x - xf) * 256.0f));
-  const int wy1 = static_cast<int>(__float2uint_rz((y - yf) * 256.0f));
-  const int wx0 = 256 - wx1, wy0 = 256 - wy1;
-  *w00 = wx0 * wy0;
-  *w10 = wx1 * wy0;
-  *w01 = wx0 * wy1;
-  *w11 = wx1 * wy1;
+  const unsigned int wx1 = __float2uint_rz((x - xf) * 65536.0f);
+  const unsigned int wy1 = __float2uint_rz((y - yf) * 65536.0f);
+  const unsigned int wx0 = 65536u - wx1, wy0 = 65536u - wy1;
+  *w00 = static_cast<unsigned long long>(wx0) * wy0;
+  *w10 = static_cast<unsigned long long>(wx1) * wy0;
+  *w01 = static_cast<unsigned long long>(wx0) * wy1;
+  *w11 = static_cast<unsigned long long>(wx1) * wy1;
+}
+
+// one corner weight w <= 2^32 into the deposit window's two 32-bit parts
+__device__ __forceinline__ void win_add(unsigned int* Dh, unsigned int* Dl, int d, unsigned long long w) {
+  const unsigned int h = static_cast<unsigned int>(w >> 16), l = static_cast<unsigned int>(w) & 0xFFFFu;
+  if (h) atomicAdd(&Dh[d], h);
+  if (l) atomicAdd(&Dl[d], l);
 }
 
 __device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
@@ -125,15 +136,16 @@ __device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
 }
 
 __device__ __forceinline__ void deposit2_global(const Dev2D& D, float x, float y, long long sign) {
-  int i, j, j1, w00, w10, w01, w11;
+  int i, j, j1;
+  unsigned long long w00, w10, w01, w11;
   deposit_weights(x, y, D.Ny, &i, &j, &j1, &w00, &w10, &w01, &w11);
   const long long di = (i == 0) ? 2 : 1, di1 = (i + 1 == D.Nx) ? 2 : 1;
   long long* G = D.G2;
   const long long r0 = static_cast<long long>(i) * D.Ny, r1 = static_cast<long long>(i + 1) * D.Ny;
-  if (w00) atomic_add_i64(&G[r0 + j], sign * di * w00);
-  if (w10) atomic_add_i64(&G[r1 + j], sign * di1 * w10);
-  if (w01) atomic_add_i64(&G[r0 + j1], sign * di * w01);
-  if (w11) atomic_add_i64(&G[r1 + j1], sign * di1 * w11);
+  if (w00) atomic_add_i64(&G[r0 + j], sign * di * static_cast<long long>(w00));
+  if (w10) atomic_add_i64(&G[r1 + j], sign * di1 * static_cast<long long>(w10));
+  if (w01) atomic_add_i64(&G[r0 + j1], sign * di * static_cast<long long>(w01));
+  if (w11) atomic_add_i64(&G[r1 + j1], sign * di1 * static_cast<long long>(w11));
 }
 
 // ---------------------------------------------------------------------------
@@ -144,7 +156,10 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         AbsRec2* __restrict__ abs_all, int abs_cap) {
   __shared__ float Exw[kW2 * kW2];
   __shared__ float Eyw[kW2 * kW2];
-  __shared__ unsigned int Dw[kW2 * kW2];
+  // deposit window: high and low 16-bit parts of the corner weights; an item
+  // of at most 32768 particles adds at most 32768 x 2^16 = 2^31 to either
+  __shared__ unsigned int Dh[kW2 * kW2];
+  __shared__ unsigned int Dl[kW2 * kW2];
   __shared__ int s_items[2 * kSpecies + 1];  // item offsets: sorted / tail per species
   __shared__ int s_abs_n, s_stop, s_over;
   __shared__ unsigned long long s_cnt[2][kSpecies];
@@ -214,7 +229,8 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         const int gy = wrapi(oy + ly, Ny);  // one wrap: Ny >= the window edge
         Exw[q] = (gx >= 0 && gx < D.Nx) ? D.Ex[static_cast<long long>(gx) * Ny + gy] : 0.0f;
         Eyw[q] = (gx >= 0 && gx <= D.Nx) ? D.Ey[static_cast<long long>(gx) * Ny + gy] : 0.0f;
-        Dw[q] = 0u;
+        Dh[q] = 0u;
+        Dl[q] = 0u;
       }
       __syncthreads();
     } else {
@@ -300,15 +316,16 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
           uv[q] = un;
           yv[q] = yn;
           wv[q] = wn;
-          int i, j, j1, w00, w10, w01, w11;
+          int i, j, j1;
+          unsigned long long w00, w10, w01, w11;
           deposit_weights(xn, yn, Ny, &i, &j, &j1, &w00, &w10, &w01, &w11);
           const int d00 = win ? win_rel(i, j, ox, oy, Ny) : -1;
           if (d00 >= 0) {
             const int d10 = d00 + kW2, d01 = d00 + 1, d11 = d10 + 1;
-            if (w00) atomicAdd(&Dw[d00], static_cast<unsigned int>(w00));
-            if (w10) atomicAdd(&Dw[d10], static_cast<unsigned int>(w10));
-            if (w01) atomicAdd(&Dw[d01], static_cast<unsigned int>(w01));
-            if (w11) atomicAdd(&Dw[d11], static_cast<unsigned int>(w11));
+            win_add(Dh, Dl, d00, w00);
+            win_add(Dh, Dl, d10, w10);
+            win_add(Dh, Dl, d01, w01);
+            win_add(Dh, Dl, d11, w11);
           } else {
             deposit2_global(D, xn, yn, sign);
           }
@@ -322,8 +339,8 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
     if (win) {  // flush the deposit window into the int64 grid
       __syncthreads();
       for (int q = threadIdx.x; q < kW2 * kW2; q += kThreads2) {
-        const unsigned int v = Dw[q];
-        if (v == 0u) continue;
+        const unsigned long long v = (static_cast<unsigned long long>(Dh[q]) << 16) + Dl[q];
+        if (v == 0ULL) continue;
         const int gx = ox + q / kW2;
         const int gy = wrapi(oy + q % kW2, Ny);
         const long long dbl = (gx == 0 || gx == D.Nx) ? 2 : 1;
@@ -374,7 +391,7 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
       const double ua = u01(wv.w[0]), ub = u01(wv.w[1]), frac = u01(wv.w[2]);
       const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
       const double use = P->see_vth * fabs(z) * dt / dx;
-      const double xd = (el == 0) ? use * frac : static_cast<double>(D.Nx) - use * frac;
+      const double xd = (el == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(D.Nx), __dmul_rn(use, frac));
       const float xr = nudge_inside<float>(xd, D.Nx);
       const unsigned long long slot = wb + static_cast<unsigned long long>(jn);
       if (slot < static_cast<unsigned long long>(P->cap[CP_SECONDARIES])) {
@@ -414,14 +431,14 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
       const double frac = u01(wv.w[0]);
       const double Eb = (P->beam_mode == 0)
                             ? P->beam_E_eV
-                            : P->beam_Emin_eV + (P->beam_Emax_eV - P->beam_Emin_eV) * u01(wv.w[1]);
+                            : __dadd_rn(P->beam_Emin_eV, __dmul_rn(__dsub_rn(P->beam_Emax_eV, P->beam_Emin_eV), u01(wv.w[1])));
       const double ub = sqrt(2.0 * Eb * P->e / P->m_i) * dt / dx;
       const double z = sqrt(-2.0 * log(u01(wv.w[2]))) * cos(2.0 * pi * u01(wv.w[3]));
       double yc = D.beam_yc + D.beam_sigma * z;
       yc -= static_cast<double>(Ny) * floor(yc / static_cast<double>(Ny));
       float yr = static_cast<float>(yc);
       if (!(yr < D.Nyf)) yr = 0.0f;
-      const float xr = nudge_inside<float>(static_cast<double>(D.Nx) - ub * frac, D.Nx);
+      const float xr = nudge_inside<float>(__dsub_rn(static_cast<double>(D.Nx), __dmul_rn(ub, frac)), D.Nx);
       const unsigned long long slot =
           wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));
       if (slot < static_cast<unsigned long long>(P->cap[CP_IONS])) {

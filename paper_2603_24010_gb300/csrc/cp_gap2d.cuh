@@ -15,6 +15,7 @@ constexpr int kH2 = 4;           // halo of the field and deposit windows in cel
 constexpr int kW2 = kT2 + 2 * kH2 + 2;  // window edge in nodes (42)
 constexpr int kChunk2 = 32768;   // particles per work item
 constexpr int kThreads2 = 512;
+constexpr double kFix2 = 4294967296.0;  // charge-grid units per macroparticle (2^16 per axis)
 
 struct Dev2D {
   int Nx, Ny, ntx, nty, T;

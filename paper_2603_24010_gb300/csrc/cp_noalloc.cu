@@ -38,7 +38,8 @@ struct Scratch {
 static __device__ __align__(256) Scratch g_scratch;
 
 // Tally slots in Scratch::counters
-enum { kListLen = 0, kSeCount = 1, kOverflow = 2, kAbs0 = 3, kAbs1 = 4, kEmit0 = 5, kEmit1 = 6, kConv = 7 };
+enum { kListLen = 0, kSeCount = 1, kOverflow = 2, kAbs0 = 3, kAbs1 = 4, kEmit0 = 5, kEmit1 = 6, kConv = 7,
+       kStatus = kCounters - 1 };
 
 struct Params {
   int N;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_see(Params p, Scratch* sc, float* 
       const double ua = u01(wv.w[0]), ub = u01(wv.w[1]), frac = u01(wv.w[2]);
       const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);
       const double use = p.see_vth * fabs(z) * p.dt / p.dx;
-      const double xd = (rec.electrode == 0) ? use * frac : static_cast<double>(N) - use * frac;
+      const double xd = (rec.electrode == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(N), __dmul_rn(use, frac));
       float xr = static_cast<float>(xd);
       if (xr >= static_cast<float>(N)) xr = nextafterf(static_cast<float>(N), 0.f);
       if (xr <= 0.f) xr = 1.17549435e-38f;
@@ -199,6 +200,22 @@ __global__ void __launch_bounds__(kThreads) k_see(Params p, Scratch* sc, float* 
       }
     }
   }
+}
+
+// The call's six counts written on the device (no host round trip): [0]
+// absorbed at x = 0, [1] absorbed at x = d, [2] emitted at x = 0, [3] emitted
+// at x = d, [4] electrons written (at most se_cap), [5] convection count at
+// x = 0.  status[0] = 1 when emitted electrons did not fit in se_cap.
+__global__ void k_counts(const Scratch* sc, int64_t se_cap, int64_t* counts, unsigned long long* status) {
+  const unsigned long long se = sc->counters[kSeCount];
+  const unsigned long long cap = static_cast<unsigned long long>(se_cap);
+  counts[0] = static_cast<int64_t>(sc->counters[kAbs0]);
+  counts[1] = static_cast<int64_t>(sc->counters[kAbs1]);
+  counts[2] = static_cast<int64_t>(sc->counters[kEmit0]);
+  counts[3] = static_cast<int64_t>(sc->counters[kEmit1]);
+  counts[4] = static_cast<int64_t>(se < cap ? se : cap);
+  counts[5] = static_cast<int64_t>(sc->counters[kAbs0]) + static_cast<int64_t>(sc->counters[kEmit0]);
+  status[0] = (sc->counters[kOverflow] || se > cap) ? 1ULL : 0ULL;
 }
 
 // Device address of the scratch array (and the push kernel's shared-memory
@@ -237,6 +254,14 @@ extern "C" int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, d
       (se_cap > 0 && (!se_xi || !se_u)) || !(dt > 0) || !(gap->d > 0) || !(gap->m_i > 0) ||
       !(gap->e > 0) || !(gap->m_e > 0) || step < 0)
     return CP_ERR_ARG;
+  // the SEE law as cp_create accepts it: a bounded mean yield keeps the
+  // per-impact draw loop and the warp scan of counts small, and a finite,
+  // non-negative emission temperature keeps the emitted positions finite
+  if (!(see->gamma_max >= 0.0 && see->gamma_max <= 14.0) || !(see->scale >= 0.0) ||
+      !std::isfinite(see->scale) || !(see->gamma_coef >= 0.0) || !std::isfinite(see->gamma_coef) ||
+      !(see->T_emit_eV >= 0.0) || !std::isfinite(see->T_emit_eV) || !(see->E_ref_eV >= 0.0) ||
+      !std::isfinite(see->E_ref_eV))
+    return CP_ERR_ARG;
   if (gap->n_cells < 2 || gap->n_cells > kMaxCells) return CP_ERR_ARG;  // shared-memory grid limit
   if (n > kMaxIons) return CP_ERR_CAPACITY;  // beyond the scratch array: every ion might be absorbed
   int dev = 0;
@@ -272,20 +297,14 @@ extern "C" int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, d
   long long* Gl = reinterpret_cast<long long*>(G);
   k_push_ions<<<grid, kThreads, 16 * (N + 1), st>>>(p, sc, E, xi, u, id, n, Gl);
   k_see<<<grid, kThreads, 0, st>>>(p, sc, se_xi, se_u, se_cap, Gl);
+  // counts on the device; one copy of the overflow flag back for the status
+  unsigned long long* flag = &sc->counters[kStatus];
+  k_counts<<<1, 1, 0, st>>>(sc, se_cap, counts, flag);
   if (cudaGetLastError() != cudaSuccess) return CP_ERR_CUDA;
-  // counts: [0] absorbed at x = 0, [1] absorbed at x = d, [2] emitted at x = 0,
-  // [3] emitted at x = d, [4] secondaries written, [5] convection count at x = 0
-  unsigned long long host[kCounters];
-  if (cudaMemcpyAsync(host, sc->counters, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  unsigned long long overflow = 0;
+  if (cudaMemcpyAsync(&overflow, flag, sizeof(overflow), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return CP_ERR_CUDA;
-  const int64_t out[6] = {static_cast<int64_t>(host[kAbs0]), static_cast<int64_t>(host[kAbs1]),
-                          static_cast<int64_t>(host[kEmit0]), static_cast<int64_t>(host[kEmit1]),
-                          static_cast<int64_t>(host[kSeCount]),
-                          static_cast<int64_t>(host[kAbs0]) + static_cast<int64_t>(host[kEmit0])};
-  if (cudaMemcpyAsync(counts, out, sizeof(out), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return CP_ERR_CUDA;
-  if (host[kOverflow] || host[kSeCount] > static_cast<unsigned long long>(se_cap)) return CP_ERR_CAPACITY;
+  if (overflow) return CP_ERR_CAPACITY;
   return CP_OK;
 }

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push(Bufs B, int do_pu
           const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
           const double vse = P->see_vth * fabs(z);
           const double use = vse * dt / dx;
-          const double xd = (rec.electrode == 0) ? use * frac : static_cast<double>(N) - use * frac;
+          const double xd = (rec.electrode == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(N), __dmul_rn(use, frac));
           const real xr = nudge_inside<real>(xd, N);
           const real ur = static_cast<real>(rec.electrode == 0 ? use : -use);
           const unsigned long long slot = wbase + static_cast<unsigned long long>(incl - nse + j);
@@ -257,10 +257,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push(Bufs B, int do_pu
           const double frac = u01(wv.w[0]);
           const double Eb = (P->beam_mode == 0)
                                 ? P->beam_E_eV
-                                : P->beam_Emin_eV + (P->beam_Emax_eV - P->beam_Emin_eV) * u01(wv.w[1]);
+                                : __dadd_rn(P->beam_Emin_eV, __dmul_rn(__dsub_rn(P->beam_Emax_eV, P->beam_Emin_eV), u01(wv.w[1])));
           const double v = sqrt(2.0 * Eb * P->e / P->m_i);
           const double ub = v * dt / dx;
-          const real xr = nudge_inside<real>(static_cast<double>(N) - ub * frac, N);
+          const real xr = nudge_inside<real>(__dsub_rn(static_cast<double>(N), __dmul_rn(ub, frac)), N);
           const unsigned long long slot =
               wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));
           if (slot < static_cast<unsigned long long>(P->cap[CP_IONS])) {
@@ -408,6 +408,46 @@ __global__ void k_source_table(const DevParams* P, double* vs, int64_t rows) {
 cudaError_t source_table_launch(const DevParams* P, double* vs, int64_t rows, cudaStream_t st) {
   const int grid = static_cast<int>((rows + 255) / 256 < 1024 ? (rows + 255) / 256 : 1024);
   k_source_table<<<grid, 256, 0, st>>>(P, vs, rows);
+  return cudaGetLastError();
+}
+
+// Initial plasma: n co-located electron/ion pairs at temperature T (the
+// paper's runs start from a loaded plasma, Sec. 3.1).  Pair k draws
+// Philox4x64-10 counter (k, 0, 0, 0) under key (seed, load tag): xi = N u0
+// (uniform in the gap), and the Box-Muller pair of u1, u2 gives the two
+// velocities, z_e th_e and z_i th_i (th = sqrt(e T / m) dt / dx, a 1D
+// Maxwellian).  Positions are rounded to the store's precision and kept
+// inside (0, N); ion ids are k.
+template <typename real>
+__global__ void k_load_pairs(real* xe, real* ue, real* xo, real* uo, uint32_t* id, int64_t n, int N,
+                             double th_e, double th_i, uint64_t seed) {
+  const double pi = 3.14159265358979323846;
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const U64x4 w = philox4x64_10(static_cast<uint64_t>(k), 0, 0, 0, seed, kTagLoad);
+    const real x = nudge_inside<real>(__dmul_rn(static_cast<double>(N), u01(w.w[0])), N);
+    const double r = sqrt(-2.0 * log(u01(w.w[1])));
+    const double a = __dmul_rn(2.0 * pi, u01(w.w[2]));
+    xe[k] = x;
+    xo[k] = x;
+    ue[k] = static_cast<real>(__dmul_rn(th_e, __dmul_rn(r, cos(a))));
+    uo[k] = static_cast<real>(__dmul_rn(th_i, __dmul_rn(r, sin(a))));
+    id[k] = static_cast<uint32_t>(k);
+  }
+}
+
+cudaError_t load_pairs_launch(int precision, void* xe, void* ue, void* xo, void* uo, uint32_t* id,
+                              int64_t n, int N, double th_e, double th_i, uint64_t seed, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+  if (precision == CP_FP32)
+    k_load_pairs<float><<<grid, 256, 0, st>>>(static_cast<float*>(xe), static_cast<float*>(ue),
+                                              static_cast<float*>(xo), static_cast<float*>(uo), id, n, N,
+                                              th_e, th_i, seed);
+  else
+    k_load_pairs<double><<<grid, 256, 0, st>>>(static_cast<double*>(xe), static_cast<double*>(ue),
+                                               static_cast<double*>(xo), static_cast<double*>(uo), id, n,
+                                               N, th_e, th_i, seed);
   return cudaGetLastError();
 }
 

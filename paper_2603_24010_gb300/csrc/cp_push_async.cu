@@ -12,6 +12,7 @@
 // half-grid values, padded by a copy of each end value (the slope is
 // recomputed from neighbours exactly as the solve forms it, and is zero past
 // either end), and the deposit uses one 32-bit sum per node.
+
 #include "cp_common.cuh"
 
 namespace cpk {
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     float* __restrict__ xs = reinterpret_cast<float*>(S->xi[s]);
     float* __restrict__ us = reinterpret_cast<float*>(S->u[s]);
     const int64_t n = S->n_proc[s];  // multiple of 4
+    if (n == 0) continue;  // the same for every thread of the CTA
     const int64_t ntiles = (n + kTile - 1) / kTile;
     const int mine = (ntiles > blockIdx.x) ? static_cast<int>((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
     const long long sign = (s == CP_IONS) ? 1LL : -1LL;
@@ -158,49 +160,52 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     for (int j = 0; j < mine; ++j, base += stride, st = (st == kAStages - 1) ? 0 : st + 1) {
       issue(j + 2 < mine);
       cp_async_wait<2>();  // this thread's copies of tile j have landed
-      if (base < n) {
-        const float4* slot = my_slot + st * (kThreads * 2);
+      const bool valid = base < n;  // the last tile's tail lanes hold no particles
+      const float4* slot = my_slot + st * (kThreads * 2);
+      if (do_push && valid) {
         const float4 xa = slot[0];
+        const float4 ua = slot[kThreads];
         float xv[4] = {xa.x, xa.y, xa.z, xa.w};
-        if (do_push) {
-          const float4 ua = slot[kThreads];
-          float uv[4] = {ua.x, ua.y, ua.z, ua.w};
+        float uv[4] = {ua.x, ua.y, ua.z, ua.w};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (xv[q] > 0.0f && xv[q] < Nr) {  // live (dead slots hold -1)
-              const float E = gather_tab(Et, xv[q]);
-              const float un = fmaf(kap, E, uv[q]);
-              const float xn = xv[q] + un;
-              cfl = max(cfl, __float_as_uint(fabsf(un)));
-              if (!(xn > 0.0f && xn < Nr)) {  // absorbed (a non-finite value counts at x = d)
-                const int el = (xn <= 0.0f) ? 0 : 1;
-                if (el) ++a1; else ++a0;
-                if (s == CP_IONS) {
-                  const int slot_i = atomicAdd(&s_abs_n, 1);
-                  if (slot_i < cap) {
-                    AbsRec r;
-                    r.id = ids[base + q];
-                    r.electrode = static_cast<uint32_t>(el);
-                    r.u = static_cast<double>(un);
-                    my_abs[slot_i] = r;
-                  }
+        for (int q = 0; q < 4; ++q) {
+          bool dep = false;
+          if (xv[q] > 0.0f && xv[q] < Nr) {  // live (dead slots hold -1)
+            const float E = gather_tab(Et, xv[q]);
+            const float un = fmaf(kap, E, uv[q]);
+            const float xn = xv[q] + un;
+            cfl = max(cfl, __float_as_uint(fabsf(un)));
+            if (!(xn > 0.0f && xn < Nr)) {  // absorbed (a non-finite value counts at x = d)
+              const int el = (xn <= 0.0f) ? 0 : 1;
+              if (el) ++a1; else ++a0;
+              if (s == CP_IONS) {
+                const int slot_i = atomicAdd(&s_abs_n, 1);
+                if (slot_i < cap) {
+                  AbsRec r;
+                  r.id = ids[base + q];
+                  r.electrode = static_cast<uint32_t>(el);
+                  r.u = static_cast<double>(un);
+                  my_abs[slot_i] = r;
                 }
-                xv[q] = -1.0f;
-                uv[q] = 0.0f;
-              } else {
-                deposit_nodes(nd, xn);
-                xv[q] = xn;
-                uv[q] = un;
               }
+              xv[q] = -1.0f;
+              uv[q] = 0.0f;
+            } else {
+              dep = true;
+              xv[q] = xn;
+              uv[q] = un;
             }
           }
-          store4(xs + base, xv);
-          store4(us + base, uv);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (xv[q] > 0.0f && xv[q] < Nr) deposit_nodes(nd, xv[q]);
+          if (dep) deposit_nodes(nd, xv[q]);
         }
+        store4(xs + base, xv);
+        store4(us + base, uv);
+      } else if (!do_push && valid) {
+        const float4 xa = slot[0];
+        const float xv[4] = {xa.x, xa.y, xa.z, xa.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (xv[q] > 0.0f && xv[q] < Nr) deposit_nodes(nd, xv[q]);
       }
       if (++since == kFlushTiles) {  // bounds every 32-bit node sum below 2^32
         __syncthreads();
@@ -266,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
           const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
           const double vse = P->see_vth * fabs(z);
           const double use = vse * dt / dx;
-          const double xd = (rec.electrode == 0) ? use * frac : static_cast<double>(N) - use * frac;
+          const double xd = (rec.electrode == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(N), __dmul_rn(use, frac));
           const float xr = nudge_inside<float>(xd, N);
           const float ur = static_cast<float>(rec.electrode == 0 ? use : -use);
           const unsigned long long slot = wbase + static_cast<unsigned long long>(incl - nse + j);
@@ -307,12 +312,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
           const U64x4 wv = philox4x64_10(static_cast<uint64_t>(kk), static_cast<uint64_t>(step), 0,
                                          0, P->seed, kTagBeam);
           const double frac = u01(wv.w[0]);
-          const double Eb = (P->beam_mode == 0)
-                                ? P->beam_E_eV
-                                : P->beam_Emin_eV + (P->beam_Emax_eV - P->beam_Emin_eV) * u01(wv.w[1]);
-          const double v = sqrt(2.0 * Eb * P->e / P->m_i);
-          const double ub = v * dt / dx;
-          const float xr = nudge_inside<float>(static_cast<double>(N) - ub * frac, N);
+          double ub = P->beam_ub;  // mono-energetic: sqrt(2 E e / m_i) dt / dx, formed on the host
+          if (P->beam_mode != 0) {
+            const double Eb = __dadd_rn(P->beam_Emin_eV,
+                                        __dmul_rn(__dsub_rn(P->beam_Emax_eV, P->beam_Emin_eV), u01(wv.w[1])));
+            ub = sqrt(2.0 * Eb * P->e / P->m_i) * dt / dx;
+          }
+          const float xr = nudge_inside<float>(__dsub_rn(static_cast<double>(N), __dmul_rn(ub, frac)), N);
           const unsigned long long slot =
               wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));
           if (slot < static_cast<unsigned long long>(P->cap[CP_IONS])) {

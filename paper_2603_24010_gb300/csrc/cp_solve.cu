@@ -297,17 +297,33 @@ __device__ __forceinline__ void level_charges(const DevParams* P, const double* 
   }
 }
 
+// The installed network is copied into shared memory while the solve scans
+// (16-byte asynchronous copies, waited for only when the network runs), so
+// that its four layers read their weights from shared memory.
+__device__ __forceinline__ void prefetch_net(const PredNet* net, PredNet* s_net) {
+  const char* src = reinterpret_cast<const char*>(net);
+  char* dst = reinterpret_cast<char*>(s_net);
+  for (size_t o = 16 * static_cast<size_t>(threadIdx.x); o < kPredNetBytes; o += 16 * kSolveThreads)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst + o))),
+                 "l"(src + o)
+                 : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // Predictor step on one CTA (all threads): append the feature row of the
-// level just solved to the 8-level window and, once the window is full,
-// evaluate the network for the next level's J_hat.
+// level just solved to the 8-level window (a ring: one row written per
+// level) and, once the window is full, evaluate the network (its copy in
+// shared memory, s_net) for the next level's J_hat.
 // (The pointers are passed one by one: a reference to the kernel's parameter
 // block would force a copy of it into local memory for the whole solve.)
-__device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, const PredNet* net,
+__device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, const PredNet* s_net,
                                               const double* sc, bool strict_rlc, double phi0) {
   __shared__ float x[kPredIn];
   __shared__ float h1[kHid], h2[kHid], h3[kHid];
   __shared__ float y[kPredOut];
-  __shared__ int s_full;
+  __shared__ double s_row[kPredFeat];
+  __shared__ int s_full, s_old;
   if (threadIdx.x == 0) {
     double Qn, sigma_n, I;
     level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
@@ -318,34 +334,39 @@ __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, c
     row[2] = sigma_n * A - sc[7] * A;  // Q_surf^n - Q_surf^{n-1}
     row[3] = sc[33];                   // secondaries emitted at x = 0
     row[4] = sc[34];                   // energy of the ions absorbed at x = 0 [eV]
-    for (int j = 0; j + 1 < kPredWindow; ++j)
-      for (int f = 0; f < kPredFeat; ++f) S->feat[j][f] = S->feat[j + 1][f];
-    for (int f = 0; f < kPredFeat; ++f) S->feat[kPredWindow - 1][f] = row[f];
+    const int pos = S->feat_pos;
+    for (int f = 0; f < kPredFeat; ++f) {
+      S->feat[pos][f] = row[f];
+      s_row[f] = row[f];
+    }
+    S->feat_pos = (pos + 1) & (kPredWindow - 1);
     const int nf = min(S->n_feat + 1, kPredWindow);
     S->n_feat = nf;
     s_full = (nf == kPredWindow);
+    s_old = (pos + 1) & (kPredWindow - 1);  // ring slot of the oldest row
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies of the network
   __syncthreads();
   if (!s_full) {
     if (threadIdx.x == 0) S->pred_ready = 0;
     return;
   }
-  if (threadIdx.x < kPredIn) {
-    const int f = threadIdx.x % kPredFeat;
-    x[threadIdx.x] = static_cast<float>(S->feat[threadIdx.x / kPredFeat][f] /
-                                        static_cast<double>(net->in_scale[f]));
+  if (threadIdx.x < kPredIn) {  // window position j (0 = oldest), feature f
+    const int j = threadIdx.x / kPredFeat, f = threadIdx.x % kPredFeat;
+    const double v = (j == kPredWindow - 1) ? s_row[f] : S->feat[(s_old + j) & (kPredWindow - 1)][f];
+    x[threadIdx.x] = static_cast<float>(v / static_cast<double>(s_net->in_scale[f]));
   }
   __syncthreads();
-  dense_one<kPredIn, kHid, true>(net->W1, net->b1, x, h1);
+  dense_one<kPredIn, kHid, true>(s_net->W1, s_net->b1, x, h1);
   __syncthreads();
-  dense_one<kHid, kHid, true>(net->W2, net->b2, h1, h2);
+  dense_one<kHid, kHid, true>(s_net->W2, s_net->b2, h1, h2);
   __syncthreads();
-  dense_one<kHid, kHid, true>(net->W3, net->b3, h2, h3);
+  dense_one<kHid, kHid, true>(s_net->W3, s_net->b3, h2, h3);
   __syncthreads();
-  dense_one<kHid, kPredOut, false>(net->W4, net->b4, h3, y);
+  dense_one<kHid, kPredOut, false>(s_net->W4, s_net->b4, h3, y);
   __syncthreads();
   if (threadIdx.x == 0) {
-    S->J_pred = static_cast<double>(net->out_scale[1]) * static_cast<double>(y[1]);
+    S->J_pred = static_cast<double>(s_net->out_scale[1]) * static_cast<double>(y[1]);
     S->pred_ready = 1;
   }
 }
@@ -375,6 +396,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   __shared__ double sc[40];
   __shared__ unsigned long long tal[11];  // the push's tallies, read early
   __shared__ int s_stop;
+  __shared__ __align__(16) PredNet s_net;  // the network, for the CTA that runs it
 
   cudaGridDependencySynchronize();  // the push that deposited G has completed
   if (threadIdx.x == 0) s_stop = (ldcg(&S->status) != 0);
@@ -393,6 +415,9 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   double* rr = bb + chunk;
 
   cudaTriggerProgrammaticLaunchCompletion();
+  // the CTA that will run the network fetches it now, behind the scan
+  const bool runs_net = (B.net != nullptr && do_push && rank == (nr > 1 ? 1 : 0));
+  if (runs_net) prefetch_net(B.net, &s_net);
   const long long G0 = ldcg(&B.G[0]);
   // G of the next chunk's first row (for the field E_hi of the gather table)
   const long long Gnext = (hi < N) ? ldcg(&B.G[hi]) : 0LL;
@@ -724,7 +749,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   // rank's remote reads are done
   cl.barrier_wait(std::move(done_tok));
   if (rank == 1) {  // the predictor runs beside rank 0's commit
-    if (B.net != nullptr && do_push) predictor_update(B.P, B.S, B.net, sc, strict_rlc, phi0_fin);
+    if (runs_net) predictor_update(B.P, B.S, &s_net, sc, strict_rlc, phi0_fin);
     return;
   }
   if (rank != 0) return;
@@ -816,9 +841,9 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     S->n_alloc[s] = na4;
     S->n_proc[s] = na4;
   }
-  if (nr == 1 && B.net != nullptr && do_push) {  // a one-CTA solve runs the predictor itself
+  if (nr == 1 && runs_net) {  // a one-CTA solve runs the predictor itself
     __syncthreads();
-    predictor_update(B.P, B.S, B.net, sc, strict_rlc, phi0_fin);
+    predictor_update(B.P, B.S, &s_net, sc, strict_rlc, phi0_fin);
   }
 }
 

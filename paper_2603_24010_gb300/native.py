@@ -21,7 +21,7 @@ SERIES_RLC, OPEN = 0, 1
 UNITS_CELL, UNITS_SI = 0, 1
 
 #: every symbol ``include/cp.h`` declares
-EXPORTS = ("cp_create", "cp_set_particles", "cp_step_strict", "cp_step_weak", "cp_read_scalars",
+EXPORTS = ("cp_create", "cp_set_particles", "cp_load_species", "cp_step_strict", "cp_step_weak", "cp_read_scalars",
            "cp_read_history", "cp_read_grid", "cp_get_particles", "cp_get_level",
            "cp_save_state", "cp_load_state", "cp_last_launch_count", "cp_enable_timing",
            "cp_read_timing", "cp_read_launch_times", "cp_push_ions_noalloc", "cp_set_predictor",
@@ -67,6 +67,11 @@ class cp_see_beam(C.Structure):
         ("beam_per_step", C.c_int32), ("beam_mode", C.c_int32)]
 
 
+class cp_species(C.Structure):
+    _fields_ = [("n0", C.c_double), ("T_load_eV", C.c_double), ("n_pairs", C.c_int64),
+                ("weight", C.c_double)]
+
+
 class cp_run(C.Structure):
     _fields_ = [("dt", C.c_double), ("seed", C.c_uint64), ("capacity", C.c_int64 * 3),
                 ("max_steps", C.c_int64), ("precision", C.c_int32), ("compact_every", C.c_int32)]
@@ -104,6 +109,7 @@ def lib():
         L.cp_create.argtypes = [C.POINTER(cp_gap), C.POINTER(cp_circuit), C.POINTER(cp_see_beam),
                                 C.POINTER(cp_run), vp, C.POINTER(vp)]
         L.cp_set_particles.argtypes = [vp, C.c_int32, dp, dp, u32p, C.c_int64, C.c_int32]
+        L.cp_load_species.argtypes = [vp, C.POINTER(cp_species), C.c_uint64]
         L.cp_step_strict.argtypes = [vp, C.c_int32, C.c_double]
         L.cp_step_weak.argtypes = [vp, C.c_int32]
         L.cp_read_scalars.argtypes = [vp, C.POINTER(cp_diag)]
@@ -222,6 +228,12 @@ def cp_set_particles(ctx, species, x, v, ids=None, units=UNITS_CELL):
     if ids is not None:
         ids = np.ascontiguousarray(ids, dtype=np.uint32)
     return lib().cp_set_particles(ctx, int(species), _dp(x), _dp(v), _u32p(ids), x.size, int(units))
+
+
+def cp_load_species(ctx, n_pairs, T_load_eV, seed, n0=0.0, weight=0.0):
+    sp = cp_species(n0=float(n0), T_load_eV=float(T_load_eV), n_pairs=int(n_pairs),
+                    weight=float(weight))
+    return lib().cp_load_species(ctx, C.byref(sp), int(seed) & (2**64 - 1))
 
 
 def cp_step_strict(ctx, n_steps, residual_tol=1e-12):
@@ -421,6 +433,10 @@ class Gap:
 
     def set_particles(self, species, xi, u, ids=None, units=UNITS_CELL):
         _check("cp_set_particles", cp_set_particles(self.ctx, species, xi, u, ids, units))
+
+    def load_species(self, n_pairs, T_load_eV, seed, n0=0.0, weight=0.0):
+        """Draw the initial co-located electron/ion pairs on the device."""
+        _check("cp_load_species", cp_load_species(self.ctx, n_pairs, T_load_eV, seed, n0, weight))
 
     def step(self, mode, n_steps, tol=1e-12):
         if mode == STRICT:

@@ -255,3 +255,45 @@ def test_a_failing_instance_stops_alone(env):
         np.testing.assert_array_equal(bb.history(i)["V_gap"], ref["h"]["V_gap"])
     assert bb.history(2)["V_gap"].size < steps + 1  # stopped early
     bb.close()
+
+
+def test_ensemble_instances_match_the_oracle(env, orc):
+    """Four uneven instances of one ensemble against the FP64 oracle run of
+    each: the level-0 charge grid bit for bit, then 300 strict steps with
+    impacts and emission, V_gap, I_circ and Q_surf within 0.5 % and the
+    cumulative event counts within the FP32 event-shift allowance."""
+    torch, native = env
+    cfgs = instances(4, seed=3, thin=400)
+    steps = 300
+    b = batch_of(native, cfgs, steps)
+    b.step(0, 0)
+    G0 = [b.grid(i)["G"].copy() for i in range(len(cfgs))]
+    b.step(0, steps)
+    assert (b.status() == 0).all()
+    emitted = 0
+    for i, cfg in enumerate(cfgs):
+        xi, ue, ui, ids = load(cfg)
+        N = cfg["n_cells"]
+        xe, ue32 = W.as_precision(xi, ue, N, W.FP32)
+        xo, ui32 = W.as_precision(xi, ui, N, W.FP32)
+        r = orc.OracleGap(cfg)
+        r.set_particles(orc.ELECTRONS, xe, ue32)
+        r.set_particles(orc.IONS, xo, ui32, ids)
+        assert r.step(orc.STRICT, 0) == orc.OK
+        np.testing.assert_array_equal(G0[i], r.grid()["G"])
+        assert r.step(orc.STRICT, steps) == orc.OK
+        hr = r.history()
+        r.close()
+        hg = b.history(i)
+        assert len(hg["V_gap"]) == len(hr["V_gap"])
+        for k in ("V_gap", "I_circ", "Q_surf"):
+            s = np.abs(hr[k]).max()
+            assert np.abs(hg[k] - hr[k]).max() <= 5e-3 * s, (i, k)
+        for a, c in ((hg["absorbed"][:, 0, 1], hr["absorbed"][:, 0, 1]),
+                     (hg["emitted"][:, 0], hr["emitted"][:, 0]),
+                     (hg["conv_count"], hr["conv_count"])):
+            ca, cb = np.cumsum(a), np.cumsum(c)
+            assert np.all(np.abs(ca - cb) <= 3 * cfg["beam_per_step"] + 0.01 * np.abs(cb)), i
+        emitted += int(hr["emitted"][:, 0].sum())
+    b.close()
+    assert emitted > 20  # the run reaches secondary emission

@@ -91,8 +91,9 @@ def test_largest_gap_that_fits(nat, orc, precision, n_cells):
         g.step(0, 1)
         assert r.step(orc.STRICT, 1) == orc.OK
         worst = max(worst, rel(g.grid()["E"], r.grid()["E"]))
-    # FP64 particles: rounding order only; FP32: the error of FP32 positions
-    assert worst < (1e-5 if precision == 0 else 2e-3), worst
+    # FP64 particles: rounding order only; FP32: the error of FP32 positions,
+    # ulp(11390) = 2^-10 cells here
+    assert worst < (1e-5 if precision == 0 else 4e-4), worst
     if precision == 0:  # same absorption decisions
         np.testing.assert_array_equal(g.history()["n_live"], r.history()["n_live"])
     with pytest.raises(nat.CpError):
@@ -151,8 +152,10 @@ def test_fields_first_100_steps_fp32(nat, orc, mode):
         assert r.step(mode, 1) == orc.OK
         worst = max(worst, rel(g.grid()["E"], r.grid()["E"]))
     hg, hr = g.history(), r.history()
-    assert worst < 2e-3, worst
-    assert rel(hg["V_gap"], hr["V_gap"]) < 1e-3
+    # FP32 positions (ulp(4096) = 2^-12 cells) carried into the deposit: a few
+    # 1e-5 of the field (about twice the largest error seen)
+    assert worst < 8e-5, worst
+    assert rel(hg["V_gap"], hr["V_gap"]) < 1e-5
 
 
 # ----------------------------------------------------------- full run, FP64
@@ -322,3 +325,37 @@ def test_error_statuses(nat):
     g3 = nat.Gap(cfg, max_steps=5)
     assert nat.cp_set_particles(g3.ctx, 1, [0.0], [0.0]) == nat.ERR_ARG  # on the wall
     assert nat.cp_step_strict(g3.ctx, 6, 1e-12) == nat.ERR_ARG  # beyond max_steps
+
+
+# ------------------------------------------------------- non-finite input
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("field,value", [("V0", float("nan")), ("V0", float("inf")),
+                                         ("weight", float("inf"))])
+def test_nonfinite_input_is_reported(nat, mode, field, value):
+    """A non-finite (or overflowing) source amplitude or weight from the host
+    makes the solve's state non-finite: the step call returns
+    CP_ERR_NONFINITE without any device fault, the context stays at the last
+    level it reached, and later calls report the same status."""
+    cfg = W.scaled(W.gap_1d_fp64(), steps=20, n_pairs=500)
+    cfg["weight"] = cfg["n0"] * cfg["d"] * cfg["area"] / cfg["n_pairs"]
+    cfg[field] = value
+    xi, ue, ui = W.load_pairs(cfg)
+    g = nat.Gap(cfg, max_steps=20)
+    g.set_particles(nat.ELECTRONS, xi, ue)
+    g.set_particles(nat.IONS, xi, ui)
+    step = (lambda n: nat.cp_step_strict(g.ctx, n, 1e-12)) if mode == 0 else \
+        (lambda n: nat.cp_step_weak(g.ctx, n))
+    assert step(10) == nat.ERR_NONFINITE
+    lv = g.level
+    assert lv < 10
+    assert step(3) == nat.ERR_NONFINITE
+    assert g.level == lv
+    g.close()
+    # the device is still usable: a new context runs normally
+    ok = W.scaled(W.gap_1d_fp64(), steps=5, n_pairs=500)
+    ok["weight"] = ok["n0"] * ok["d"] * ok["area"] / ok["n_pairs"]
+    g2 = nat.Gap(ok, max_steps=5)
+    g2.set_particles(nat.ELECTRONS, xi, ue)
+    g2.set_particles(nat.IONS, xi, ui)
+    assert nat.cp_step_strict(g2.ctx, 5, 1e-12) == nat.OK
+    g2.close()

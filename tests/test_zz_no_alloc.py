@@ -125,3 +125,43 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     rc = native.cp_push_ions_noalloc(big, see, cfg["dt"], 0, 0, 1, dummy, dummy, dummy, dummy, 0,
                                      dummy, dummy, dummy, 8, dummy, None)
     assert rc == native.ERR_ARG
+    # SEE laws that cp_create refuses are refused before any GPU work
+    for field, bad in (("gamma_max", 15.0), ("gamma_max", float("nan")), ("scale", -1.0),
+                       ("scale", float("inf")), ("T_emit_eV", -2.0), ("T_emit_eV", float("nan")),
+                       ("gamma_coef", float("nan"))):
+        s2 = native.cp_see_beam(**{k: getattr(see, k) for k, _ in native.cp_see_beam._fields_})
+        setattr(s2, field, bad)
+        rc = native.cp_push_ions_noalloc(gap, s2, cfg["dt"], 0, 0, 1, dummy, dummy, dummy, dummy,
+                                         4, dummy, dummy, dummy, 8, dummy, None)
+        assert rc == native.ERR_ARG, (field, bad)
+
+
+def test_noalloc_reports_only_the_electrons_it_wrote(env):
+    """With too small an output array the call fails with CP_ERR_CAPACITY and
+    counts[4] gives the electrons actually written (se_cap), not the number
+    the impacts asked for (counts[2] + counts[3])."""
+    torch, native = env
+    cfg = W.scaled(W.gap_1d_fp64(seed=5), beam_per_step=0, see_scale=20.0, precision=W.FP32)
+    xi, u, ids = ion_set(cfg, 17, 2000)
+    ref = context_step(native, cfg, xi, u, ids)
+    dev = torch.device("cuda")
+    N = cfg["n_cells"]
+    gap, _, see, _ = native.structs_from_config(cfg)
+    x_t = torch.tensor(xi, dtype=torch.float32, device=dev)
+    u_t = torch.tensor(u, dtype=torch.float32, device=dev)
+    id_t = torch.tensor(ids.view(np.int32), dtype=torch.int32, device=dev)
+    E_t = torch.tensor(ref["E0"], dtype=torch.float64, device=dev)
+    G_t = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+    cap = 64
+    sx = torch.zeros(cap, dtype=torch.float32, device=dev)
+    su = torch.zeros(cap, dtype=torch.float32, device=dev)
+    counts = torch.zeros(6, dtype=torch.int64, device=dev)
+    rc = native.cp_push_ions_noalloc(gap, see, cfg["dt"], cfg["seed"], 0, 1, E_t.data_ptr(),
+                                     x_t.data_ptr(), u_t.data_ptr(), id_t.data_ptr(), xi.size,
+                                     G_t.data_ptr(), sx.data_ptr(), su.data_ptr(), cap,
+                                     counts.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == native.ERR_CAPACITY
+    c = counts.cpu().numpy()
+    assert c[2] + c[3] > cap
+    assert c[4] == cap
+    assert c[2] == ref["h"]["emitted"][0, 0] and c[3] == ref["h"]["emitted"][0, 1]
