@@ -2,12 +2,17 @@
 
 A step is one pass of the whole hot path (gather, push, absorption + SEE,
 beam injection, deposit, coupled Poisson/circuit solve) over the large FP32
-1D gap workload: 4096 cells, 1e7 macroparticles at start (5e6 e-/H+ pairs),
-5000 beam ions per step, dt = 0.5 ps, strict coupling.  The metric is
-particle-steps/s = sum over timed steps of the live macroparticles pushed in
-that step / timed seconds.  Prints one JSON line.
+1D gap workload: 4096 cells, 1e7 macroparticles at start (5e6 e-/H+ pairs
+drawn on the device), 5000 beam ions per step, dt = 0.5 ps, strict coupling.
+The gap is advanced outside the timed region to a steady-state level
+(--start-level, default 12000: the beam fills the gap, about 3e7 live
+particles, ion impacts and SEE at the cathode every step), then W warm-up and
+K timed steps follow.  The metric is particle-steps/s = sum over timed steps
+of the live macroparticles pushed in that step / timed seconds.  Prints one
+JSON line.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--start-level L]
+                    [--impl native|reference]
 
 After the timed run (outside it), the learned weak-coupling predictor is
 trained on 2048 strict runs of the same gap distribution (generated as one
@@ -90,12 +95,34 @@ def profiled_dram_bytes_per_particle():
         return None
 
 
-def workload_desc(cfg, K, W_):
-    return ("%s: %d cells, %d e-/H+ pairs loaded, %d beam ions/step (%s), dt %.3g s, "
-            "%s particles, strict coupling; %d warm-up + %d timed steps from t = 0"
+def workload_desc(cfg, K, W_, L0):
+    where = ("advanced to level %d outside the timed region (steady state: the beam across the "
+             "gap, ion impacts and SEE at the cathode), then %d warm-up + %d timed steps"
+             % (L0, W_, K)) if L0 else ("%d warm-up + %d timed steps from t = 0" % (W_, K))
+    return ("%s: %d cells, %d e-/H+ pairs loaded on the device (1 eV Maxwellian), %d beam "
+            "ions/step (%s), dt %.3g s, %s particles, strict coupling; %s"
             % (cfg["name"], cfg["n_cells"], cfg["n_pairs"], cfg["beam_per_step"],
                "mono 20 keV" if cfg["beam_mode"] == 0 else "uniform 5-50 keV", cfg["dt"],
-               "FP32" if cfg["precision"] == W.FP32 else "FP64", W_, K))
+               "FP32" if cfg["precision"] == W.FP32 else "FP64", where))
+
+
+def cpu_model():
+    """The host CPU's model name (x86 'model name', else Arm implementer/part)."""
+    info = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in info:
+        return info["model name"]
+    if "CPU implementer" in info:
+        return "Arm implementer %s part %s" % (info["CPU implementer"], info.get("CPU part", "?"))
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # ---------------------------------------------------------------- clocks
@@ -107,23 +134,33 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.gpu = gpu_index
+        self.gpu = str(gpu_index)
         self.proc = None
         self.file = None
+        self.why = None
+        try:  # the physical GPU by UUID (a logical index can differ under CUDA_VISIBLE_DEVICES)
+            import torch
+            uuid = getattr(torch.cuda.get_device_properties(gpu_index), "uuid", None)
+            if uuid:
+                u = str(uuid)
+                self.gpu = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
 
     def start(self):
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.file, stderr=subprocess.DEVNULL)
-        except Exception:
+        except Exception as e:
             self.proc = None
+            self.why = "nvidia-smi did not start: %s" % e
 
     def stop(self):
         if not self.proc:
-            return None
+            return {"samples": 0, "why": self.why} if self.why else None
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -145,9 +182,10 @@ class ClockSampler:
             except (ValueError, IndexError):
                 continue
         if not sm:
-            return None
+            return {"samples": 0, "gpu": self.gpu,
+                    "why": "nvidia-smi returned no rows for this GPU during the region"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu": self.gpu}
 
 
 def measured_peaks():
@@ -180,28 +218,35 @@ def reduce_over_ranks(ms, e2e_ms, psteps, e2e_psteps, device):
 
 
 def run_native(args, rank, world):
+    """The large gap through the C ABI: the initial plasma drawn on the device
+    (cp_load_species), advanced outside the timed region to the start level,
+    then W warm-up and K timed steps (CUDA-graph replays); K more steps with
+    per-launch CUDA events give each kernel's device time; the t = 0 window
+    and the end-to-end job are measured beside them."""
     import torch
     from paper_2603_24010_gb300 import native
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cfg = workload(args.workload, seed=args.seed + rank, pairs=args.pairs)
-    K, Wm = args.steps, args.warmup
-    total_steps = Wm + K
-    xe, ue, xI, ui = load_particles(cfg, cfg["seed"])
+    K, Wm, L0 = args.steps, args.warmup, args.start_level
     stream = torch.cuda.current_stream()
+    bpp = BYTES_PER_PARTICLE_STEP[cfg["precision"]]
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
+    def make(max_steps):
+        g = native.Gap(cfg, max_steps=max_steps, stream=stream.cuda_stream)
+        g.load_species(cfg["n_pairs"], cfg["T_load_eV"], cfg["seed"])
+        return g
+
     # ---- device-resident timed region (graph replays, the user's path) ------
-    g = native.Gap(cfg, max_steps=total_steps + 1, stream=stream.cuda_stream)
-    g.set_particles(native.ELECTRONS, xe, ue)
-    g.set_particles(native.IONS, xI, ui)
-    g.step(0, Wm)  # includes the upload, the level-0 solve and W warm-up steps
+    g = make(L0 + Wm + 2 * K + 1)
     clocks = ClockSampler(dev)
-    clocks.start()
+    clocks.start()  # sampled over the advance (seconds of load) and the timed steps
+    g.step(0, L0 + Wm)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -211,75 +256,97 @@ def run_native(args, rank, world):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
     launches = native.cp_last_launch_count(g.ctx)
-    hist = g.history(Wm, K)  # rows of levels W..W+K-1: particles pushed by the timed steps
+    hist = g.history(L0 + Wm, K)  # rows of the timed levels: particles pushed by the timed steps
     live = hist["n_live"].sum(axis=1)
     psteps = int(live.sum())
-    g.close()
+    impacts = int(hist["absorbed"][:, 0, 1].sum())
+    emitted = int(hist["emitted"].sum())
     if args.single:  # one graph pass only (used under ncu)
+        clk = clocks.stop()
+        g.close()
         return dict(cfg=cfg, ms=ms, psteps=psteps, launches=launches, clocks=clk)
 
-    # ---- the same run with per-launch CUDA events (direct launches) --------
-    # gives each kernel's device time for the roofline
-    g = native.Gap(cfg, max_steps=total_steps + 1, stream=stream.cuda_stream)
-    g.set_particles(native.ELECTRONS, xe, ue)
-    g.set_particles(native.IONS, xI, ui)
-    g.step(0, Wm)
+    # ---- K more steps of the same gap with per-launch CUDA events -----------
     native.cp_enable_timing(g.ctx, True)
     torch.cuda.synchronize()
-    t0e = torch.cuda.Event(enable_timing=True)
-    t1e = torch.cuda.Event(enable_timing=True)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0e.record(stream)
     g.step(0, K)
     t1e.record(stream)
     torch.cuda.synchronize()
     ms_timed = t0e.elapsed_time(t1e)
     kms, kn = native.cp_read_timing(g.ctx)
-    per_launch_ms = native.cp_read_launch_times(g.ctx)
+    per_launch_ms = np.asarray(native.cp_read_launch_times(g.ctx))
+    native.cp_enable_timing(g.ctx, False)
+    live_t = g.history(L0 + Wm + K, K)["n_live"].sum(axis=1)
+    clk = clocks.stop()
     g.close()
 
-    # ---- end-to-end through the C ABI with host buffers ---------------------
+    # ---- the first K steps from t = 0 (a second figure) ---------------------
+    g0 = make(Wm + K + 1)
+    g0.step(0, Wm)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    g0.step(0, K)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_t0 = a0.elapsed_time(a1)
+    psteps_t0 = int(g0.history(Wm, K)["n_live"].sum())
+    g0.close()
+
+    # ---- end to end through the C ABI: the whole job a user runs ------------
+    # cp_create + cp_load_species (parameters from host structs), every step up
+    # to the end of the timed window, and the read-back of every level's
+    # diagnostics row into host memory
+    n_all = L0 + Wm + K
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    g2 = native.Gap(cfg, max_steps=total_steps + 1, stream=stream.cuda_stream)
-    g2.set_particles(native.ELECTRONS, xe, ue)
-    g2.set_particles(native.IONS, xI, ui)
-    g2.step(0, K)
-    h2 = native.cp_read_history(g2.ctx, 0, K + 1)
+    g2 = make(n_all + 1)
+    g2.step(0, n_all)
+    h2 = native.cp_read_history(g2.ctx, 0, n_all + 1)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    e2e_psteps = int(sum(sum(h2[k].n_live) for k in range(K)))
+    e2e_psteps = int(sum(sum(h2[k].n_live) for k in range(n_all)))
     g2.close()
-    es = 4 if cfg["precision"] == W.FP32 else 8
-    h2d = (xe.size + xI.size) * 2 * es + xI.size * 4
-    d2h = (K + 1) * ctypes.sizeof(native.cp_diag)
+    h2d = sum(ctypes.sizeof(c) for c in (native.cp_gap, native.cp_circuit, native.cp_see_beam,
+                                          native.cp_run, native.cp_species))
+    d2h = (n_all + 1) * ctypes.sizeof(native.cp_diag)
 
     if world > 1:
         ms, e2e_ms, psteps, e2e_psteps = reduce_over_ranks(ms, e2e_s * 1e3, psteps, e2e_psteps, "cuda")
     else:
         e2e_ms = e2e_s * 1e3
     peak, peak_kind = measured_peaks()
-    bpp = BYTES_PER_PARTICLE_STEP[cfg["precision"]]
-    # Roofline of the step kernel: algorithmic bytes per launch / launch time,
-    # over the launches whose particle state (xi, u) exceeds 1.5 x the 129 MB
-    # L2, so that no launch can be served from L2.
-    state = live * bpp / 2
+    # Roofline of the push: algorithmic bytes per launch / launch time, over the
+    # launches whose particle state (xi, u) exceeds 1.5 x the 129 MB L2
+    state = live_t * bpp / 2
     sel = state > 1.5 * 129e6
+    all_above = bool(sel.all())
     if not sel.any():
         sel = np.ones_like(sel)
     n_sel = int(sel.sum())
-    sel_ms = float(np.asarray(per_launch_ms)[sel[:len(per_launch_ms)]].sum())
+    sel_ms = float(per_launch_ms[:len(sel)][sel[:len(per_launch_ms)]].sum())
     avg_launch_ms = sel_ms / n_sel
-    achieved = bpp * float(live[sel].sum()) / (sel_ms * 1e-3) / 1e9
+    achieved = bpp * float(live_t[sel].sum()) / (sel_ms * 1e-3) / 1e9
     dbpp = profiled_dram_bytes_per_particle() if cfg["precision"] == W.FP32 else None
-    traffic = dbpp * float(live[sel].sum()) / n_sel if dbpp else None
-    return dict(cfg=cfg, ms=ms, ms_timed=ms_timed, psteps=psteps, e2e_ms=e2e_ms, e2e_psteps=e2e_psteps, h2d=h2d,
-                d2h=d2h, launches=launches, kernel_ms=kms.tolist(), kernel_n=kn.tolist(),
-                avg_launch_ms=avg_launch_ms, achieved=achieved, peak=peak, peak_kind=peak_kind,
-                clocks=clk, bpp=bpp, n_sel=n_sel, traffic=traffic, frac_psteps_above_l2=float(live[state > 129e6].sum()) / max(psteps, 1))
+    traffic = dbpp * float(live_t[sel].sum()) / n_sel if dbpp else None
+    smin, smax = float((live * bpp / 2).min()) / 1e6, float((live * bpp / 2).max()) / 1e6
+    l2 = ("particle state (x, u) %.0f-%.0f MB over the timed steps, %s the 129 MB L2; no flush"
+          % (smin, smax, "above" if smin > 129 else ("partly above" if smax > 129 else "within")))
+    if not all_above:
+        l2 += ("; roofline over %s launches (state above 1.5 x L2 in %d of %d)"
+               % ("all" if n_sel == len(state) else "those", int((state > 1.5 * 129e6).sum()),
+                  len(state)))
+    return dict(cfg=cfg, ms=ms, ms_timed=ms_timed, psteps=psteps, e2e_ms=e2e_ms,
+                e2e_psteps=e2e_psteps, h2d=h2d, d2h=d2h, launches=launches,
+                kernel_ms=kms.tolist(), kernel_n=kn.tolist(), avg_launch_ms=avg_launch_ms,
+                achieved=achieved, peak=peak, peak_kind=peak_kind, clocks=clk, bpp=bpp,
+                n_sel=n_sel, traffic=traffic, l2=l2, impacts=impacts, emitted=emitted,
+                live_mean=float(live.mean()), ms_t0=ms_t0, psteps_t0=psteps_t0, n_all=n_all)
 
 
 # ---------------------------------------------------------------- ensemble
@@ -583,7 +650,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default 20000; 10000 for the ensemble)")
+                    help="timed steps (default 2000; 10000 for the ensemble)")
+    ap.add_argument("--start-level", type=int, default=12000,
+                    help="level the large gap is advanced to before the timed window "
+                         "(outside the timed region; 0 times from t = 0)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--workload", default="gap_1d_fp32_large")
@@ -618,27 +688,25 @@ def main():
         gap2d_main(args, {"parallelism": "1 GPU"})
         return
     if args.steps is None:
-        args.steps = 20000
+        args.steps = 2000
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     cfg = workload(args.workload, args.seed, pairs=args.pairs)
-    config = {"workload": workload_desc(cfg, args.steps, args.warmup),
-              "l2": ("inputs larger than L2 for the roofline launches (particle state > 1.5 x "
-                     "129 MB); the state starts at %.0f MB and grows with the beam, no flush"
-                     % (cfg["n_pairs"] * 2 * 2 * (4 if cfg["precision"] == W.FP32 else 8) / 1e6)),
+    config = {"workload": workload_desc(cfg, args.steps, args.warmup, args.start_level),
               "parallelism": ("replicas x%d (independent seeds)" % world) if world > 1 else "1 GPU"}
 
     if args.impl == "reference":
         if rank != 0:
             return
         value, desc = oracle_sample(cfg, args.steps, args.warmup, budget_s=120.0)
+        config["l2"] = "not applicable (host cores)"
         line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": getattr(oracle_sample, "ms_per_step", None),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config, "impl": "reference",
                 "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
-                                 "kind": "oracle", "sample": desc},
+                                 "cpu_model": cpu_model(), "kind": "oracle", "sample": desc},
                 "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -662,12 +730,15 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:  # the oracle is timed beside one GPU only
         v, desc = oracle_sample(cfg, 200, 3, budget_s=20.0)
-        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": desc}
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "cpu_model": cpu_model(),
+               "kind": "oracle", "sample": desc}
     # the predictor study is a single-GPU experiment: replica runs skip it
     coupling = None if (args.no_coupling or world > 1) else run_coupling(args)
     K = args.steps
     value = r["psteps"] / (r["ms"] * 1e-3)
+    config["l2"] = r["l2"]
+    clk = r["clocks"] or {}
+    cycles = (r["avg_launch_ms"] * 1e-3 * clk["sm_mhz"] * 1e6) if clk.get("sm_mhz") else None
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": r["ms"] / K, "higher_is_better": True,
@@ -675,7 +746,11 @@ def main():
         "dtype": "f32" if r["cfg"]["precision"] == W.FP32 else "f64", "data": "synthetic",
         "config": config,
         "e2e": {"value": r["e2e_psteps"] / (r["e2e_ms"] * 1e-3), "unit": "particle-steps/s",
-                "h2d_bytes_per_step": r["h2d"] / K, "d2h_bytes_per_step": r["d2h"] / K},
+                "h2d_bytes_per_step": r["h2d"] / r["n_all"], "d2h_bytes_per_step": r["d2h"] / r["n_all"],
+                "job": "cp_create + cp_load_species (initial plasma drawn on the device from host "
+                       "parameter structs) + %d strict steps + read-back of every level's "
+                       "diagnostics row into host memory; particle-steps of all %d steps"
+                       % (r["n_all"], r["n_all"])},
         "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
                      "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": r["traffic"],
@@ -686,12 +761,17 @@ def main():
                      "solve_avg_ms": r["kernel_ms"][1] / max(r["kernel_n"][1], 1),
                      "removal_avg_ms": r["kernel_ms"][2] / max(r["kernel_n"][2], 1),
                      "timed_pass_ms_per_step": r["ms_timed"] / K,
-                     "source": "per-launch CUDA events in a second pass over the same steps"},
+                     "push_sm_cycles_per_launch": cycles,
+                     "source": "per-launch CUDA events over the %d steps after the timed window "
+                               "(same gap, direct launches)" % K},
         "clocks": r["clocks"],
         "cpu_baseline": cpu,
         "coupling": coupling,
         "particle_steps": r["psteps"],
-        "frac_particle_steps_state_above_l2": r["frac_psteps_above_l2"],
+        "window": {"start_level": args.start_level, "live_mean": r["live_mean"],
+                   "ion_impacts_per_step": r["impacts"] / K, "secondaries_per_step": r["emitted"] / K},
+        "t0_window": {"value": r["psteps_t0"] / (r["ms_t0"] * 1e-3), "ms_per_step": r["ms_t0"] / K,
+                      "note": "the same K steps timed from t = 0 (1e7 particles, no impacts yet)"},
     }
     print(json.dumps(line))
     if world > 1:
