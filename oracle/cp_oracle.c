@@ -139,6 +139,19 @@ int64_t or_see_count(const or_params* p, double E_ion_eV, uint64_t id, int64_t s
   uint64_t ctr[4] = {id, (uint64_t)step, 0, 0}, key[2] = {p->seed, OR_TAG_SEE}, w[4];
   or_philox4x64_10(ctr, key, w);
   double u1 = or_u01(w[0]);
+  if (p->see_count_law == OR_SEE_COUNT_POISSON) {
+    /* Algorithm see_sampling_1d: n ~ Poisson(gamma), by inversion of the
+       distribution function with the same draw (the smallest n whose
+       cumulative probability exceeds u1), truncated at OR_SEE_POISSON_MAX */
+    double pk = exp(-g), F = pk;
+    int64_t n = 0;
+    while (u1 >= F && n < OR_SEE_POISSON_MAX) {
+      n += 1;
+      pk = pk * g / (double)n;
+      F = F + pk;
+    }
+    return n;
+  }
   double fl = floor(g);
   return (int64_t)fl + ((u1 < g - fl) ? 1 : 0);
 }
@@ -155,7 +168,13 @@ void or_see_electron(const or_params* p, uint64_t id, int64_t step, int64_t j, d
   or_philox4x64_10(ctr, key, w);
   double ua = or_u01(w[0]), ub = or_u01(w[1]);
   double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);
-  *v_out = sqrt(p->e * p->T_emit_eV / p->m_e) * fabs(z);
+  if (p->see_energy_law == OR_SEE_ENERGY_LOGNORMAL) {
+    /* Algorithm see_sampling_1d: E_SE ~ Lognormal(mu, sigma), v = sqrt(2 E / m_e) */
+    const double E_eV = exp(p->see_ln_mu + p->see_ln_sigma * z);
+    *v_out = sqrt(2.0 * E_eV * p->e / p->m_e);
+  } else {
+    *v_out = sqrt(p->e * p->T_emit_eV / p->m_e) * fabs(z);
+  }
   *frac_out = or_u01(w[2]);
 }
 

@@ -74,12 +74,22 @@ typedef struct {
      Q1..Q5 of Eqs. loop_1-loop_5; the gap is the load capacitor C3 (its
      charge is Q4), C1 is pre-charged to V1 at t = 0 */
   double tR1, tR2, tR3, tC1, tC2, tC3, tL1, tL2, tM, tV1;
+  /* SEE laws of Algorithm see_sampling_1d (see_count_law / see_energy_law) */
+  double see_ln_mu, see_ln_sigma; /* lognormal SE energy: ln(E / 1 eV) ~ N(mu, sigma^2) */
   uint64_t seed;
   int64_t n_cells;       /* N: nodes 0..N, phi_N = 0 */
   int64_t circuit;       /* OR_CIRCUIT_* */
   int64_t beam_per_step; /* beam macroparticles appended per step */
   int64_t beam_mode;     /* 0 mono-energetic, 1 uniform in [Emin, Emax] */
+  int64_t see_count_law;  /* 0 floor + Bernoulli, 1 Poisson (OR_SEE_*) */
+  int64_t see_energy_law; /* 0 half-Maxwellian of T_emit, 1 lognormal */
 } or_params;
+
+#define OR_SEE_COUNT_BERNOULLI 0 /* floor(gamma) + Bernoulli(gamma - floor(gamma)) */
+#define OR_SEE_COUNT_POISSON 1   /* Poisson(gamma), Algorithm see_sampling_1d */
+#define OR_SEE_POISSON_MAX 64    /* truncation of the Poisson count */
+#define OR_SEE_ENERGY_MAXWELL 0  /* |N(0,1)| sqrt(e T_emit / m_e) */
+#define OR_SEE_ENERGY_LOGNORMAL 1 /* E = exp(mu + sigma N(0,1)) eV, v = sqrt(2 E e / m_e) */
 
 /* Per-level diagnostics record: level n is written by the solve at t_n. */
 typedef struct {

@@ -23,9 +23,11 @@ class OrParams(C.Structure):
         "d", "area", "eps0", "e", "m_e", "m_i", "R", "L", "C", "V0", "f", "tau",
         "polarity", "gamma_coef", "gamma_max", "E_ref_eV", "see_scale", "T_emit_eV",
         "beam_E_eV", "beam_Emin_eV", "beam_Emax_eV", "dt", "weight", "sigma0", "grid_units",
-        "tR1", "tR2", "tR3", "tC1", "tC2", "tC3", "tL1", "tL2", "tM", "tV1")] + [
+        "tR1", "tR2", "tR3", "tC1", "tC2", "tC3", "tL1", "tL2", "tM", "tV1",
+        "see_ln_mu", "see_ln_sigma")] + [
         ("seed", C.c_uint64), ("n_cells", C.c_int64), ("circuit", C.c_int64),
-        ("beam_per_step", C.c_int64), ("beam_mode", C.c_int64)]
+        ("beam_per_step", C.c_int64), ("beam_mode", C.c_int64), ("see_count_law", C.c_int64),
+        ("see_energy_law", C.c_int64)]
 
 
 class OrDiag(C.Structure):
@@ -67,6 +69,11 @@ def lib():
                                             dp, dp]
         L.or_load_pairs.argtypes = [C.POINTER(OrParams), C.c_int64, C.c_double, C.c_uint64, dp, dp,
                                     dp]
+        L.or_tesla_matrix.argtypes = [C.POINTER(OrParams), C.c_int, dp]
+        L.or_tesla_rhs.argtypes = [C.POINTER(OrParams), dp, dp]
+        L.or_solve5.argtypes = [dp, dp, dp]
+        L.or_tesla_step.argtypes = [C.POINTER(OrParams), dp]
+        L.or_tesla_state.argtypes = [C.c_void_p, dp]
         L.or_create.argtypes = [C.POINTER(OrParams)]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
@@ -192,6 +199,32 @@ def load_pairs(cfg, n, T_eV, seed):
     return xi, ue, ui
 
 
+def tesla_matrix(cfg, coupled=False):
+    """The BDF2 circuit matrix of the Tesla loops (5 x 5)."""
+    p = make_params(cfg)
+    T = np.zeros(25)
+    lib().or_tesla_matrix(C.byref(p), int(bool(coupled)), _dp(T))
+    return T.reshape(5, 5)
+
+
+def tesla_run(cfg, steps, Q0=None):
+    """The Tesla circuit alone for `steps` BDF2 steps from rest in the state
+    Q0 (default: only C1 charged, to tV1): loop charges (steps + 1, 5), row 0
+    the initial state."""
+    p = make_params(cfg)
+    Qh = np.zeros((4, 5))
+    if Q0 is None:
+        Qh[:, 0] = cfg["tC1"] * cfg["tV1"]
+    else:
+        Qh[:] = np.asarray(Q0, np.float64)[None, :]
+    out = [Qh[0].copy()]
+    for _ in range(int(steps)):
+        if lib().or_tesla_step(C.byref(p), _dp(Qh)) != OK:
+            raise ValueError("or_tesla_step failed")
+        out.append(Qh[0].copy())
+    return np.array(out)
+
+
 def solve_fields(cfg, mode, G, conv_count, sigma_prev, Qhist, t, tol=1e-12, phi0_prev=0.0,
                  J_hat=0.0):
     p = make_params(cfg)
@@ -299,6 +332,11 @@ class OracleGap:
 
     def n_live(self, species):
         return lib().or_n_live(self._s, species)
+
+    def tesla_state(self):
+        Q = np.zeros(5)
+        lib().or_tesla_state(self._s, _dp(Q))
+        return Q
 
     def particles(self, species):
         n = self.n_live(species)

@@ -24,6 +24,15 @@ injection profile are not available, so these parameter sets stand in):
   profile (sigma 0.5 mm, centred) at n_pairs/1000 ions per step, dt = 1 ps,
   2000 steps, FP32 particles; the electrode area (depth x 5 mm) keeps the
   gap capacitance at C.
+* ``tesla_gap``: the paper's integrated configuration (Tables 3 and 4): an
+  80 mm gap of 600 cells driven by the 5-loop Tesla transformer (C1 = 3.8 uF
+  pre-charged to 3 kV, L1 = 47 uH, L2 = 0.13 H, k = 0.37, R1 = R2 = 5 Ohm,
+  R3 = 100 MOhm, C2 = 2.8 pF, the gap being the load capacitor C3 = 0.2 pF),
+  dt = 15 ns, Ti+ ions (7.95e-26 kg), electrons 1000 times heavier than
+  physical (the paper's reduced mass ratio), superparticle weight 2.5e7; the
+  paper's Gaussian ion pulse has no published profile, so a 100 eV Ti+ beam
+  of 20 macroparticles per step enters at x = d, plus 500 pairs of 1 eV
+  plasma.
 * ``ensemble``: independent 5 mm gaps with cells log-uniform in 256-4096,
   initial macroparticles log-uniform in 1e4-2e6, V0 uniform in 50-200 kV,
   C uniform in 20-500 pF, SEE scale uniform in 0-2 (every 8th instance
@@ -52,6 +61,11 @@ def _base(n_cells, n_pairs, dt, steps, beam_per_step, precision, seed=0, n0=1e14
         d=d, area=area, eps0=EPS0, e=E_CHARGE, m_e=M_E, m_i=M_P,
         R=50.0, L=1e-6, C=C, V0=100e3, f=1e6, tau=2e-6, polarity=-1.0,
         gamma_coef=0.05, gamma_max=3.0, E_ref_eV=1000.0, see_scale=1.0, T_emit_eV=2.0,
+        # SEE laws: count 0 floor + Bernoulli, 1 Poisson; energy 0 half-Maxwellian of
+        # T_emit, 1 lognormal.  The paper's lognormal parameters are not published:
+        # mu = 1.0, sigma = 0.8 (ln eV) are placeholders (mode 1.4 eV, median 2.7 eV,
+        # inside the below-20-eV regime the paper describes).
+        see_count_law=0, see_energy_law=0, see_ln_mu=1.0, see_ln_sigma=0.8,
         beam_E_eV=20e3, beam_Emin_eV=5e3, beam_Emax_eV=50e3,
         dt=dt, weight=weight, sigma0=0.0, seed=seed,
         n_cells=n_cells, circuit=0, beam_per_step=beam_per_step, beam_mode=0,
@@ -81,6 +95,31 @@ def gap_1d_fp32_thinned(seed=0, factor=25, steps=20000):
     rng = np.random.default_rng([seed, 0xBEA])
     cfg["beam_mode"] = int(rng.integers(0, 2))
     cfg["name"] = "gap_1d_fp32_thinned"
+    return cfg
+
+
+def tesla_circuit(dt):
+    """The Tesla transformer of Table 3 (loop-charge parameters tR1..tV1)."""
+    L1, L2, k = 47e-6, 0.13, 0.37
+    return dict(dt=dt, circuit=2, tR1=5.0, tR2=5.0, tR3=100e6, tC1=3.8e-6, tC2=2.8e-12,
+                tC3=0.2e-12, tL1=L1, tL2=L2, tM=k * math.sqrt(L1 * L2), tV1=3000.0)
+
+
+def tesla_gap(seed=0, steps=575):
+    """The paper's integrated configuration with the Tesla circuit (FP64)."""
+    cfg = _base(600, 500, 15e-9, steps, 20, FP64, seed)
+    cfg.update(tesla_circuit(15e-9))
+    cfg["d"] = 0.08
+    cfg["C"] = cfg["tC3"]
+    cfg["area"] = cfg["tC3"] * cfg["d"] / EPS0  # the particle-free gap is C3
+    cfg["m_i"] = 7.95e-26  # Ti+
+    cfg["m_e"] = 1000.0 * M_E  # reduced mass ratio
+    cfg["weight"] = 2.5e7
+    cfg["beam_E_eV"] = 100.0
+    # the paper's SEE sampling: Poisson counts, lognormal energies
+    cfg["see_count_law"], cfg["see_energy_law"] = 1, 1
+    cfg["see_scale"] = 8.0
+    cfg["name"] = "tesla_gap"
     return cfg
 
 
