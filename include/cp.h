@@ -62,6 +62,7 @@ extern "C" {
 
 #define CP_CIRCUIT_SERIES_RLC 0 /* L Q'' + R Q' + V_gap = polarity V_s(t) */
 #define CP_CIRCUIT_OPEN 1       /* floating driven electrode: Q_circ constant */
+#define CP_CIRCUIT_TESLA 2      /* the paper's 5-loop Tesla transformer (cp_tesla) */
 
 #define CP_UNITS_CELL 0 /* xi = x/dx, u = v dt/dx */
 #define CP_UNITS_SI 1   /* x [m], v [m/s] */
@@ -83,30 +84,70 @@ typedef struct {
   int32_t pad0;
 } cp_gap;
 
-/* External circuit (Sec. 2.1, App. A): a series R-L loop with the source
-   V_s(t) = V0 (1 - cos 2 pi f t) exp(-t/tau) / 2 driving the x = 0 electrode
-   with sign `polarity`; C is the load capacitance used by the weak scheme's
-   free circuit solve (Sec. 2.4.3) and to derive A when area == 0. */
+/* The simplified Tesla transformer of Sec. 2.1 (Eqs. loop_1-loop_5, the
+   parameters of Table 3): loop charges Q1..Q5 with
+     Q1/C1 + R1 (Q1 - Q2 - Q5)' = 0
+     R1 (-Q1 + Q2 + Q5)' + R2 Q2' + L1 Q2'' + M Q3'' = 0
+     M Q2'' + L2 Q3'' + R3 (Q3 - Q4 + Q5)' = 0
+     R3 (-Q3 + Q4 - Q5)' + V_C3 = 0           (V_C3 = Q4/C3 alone; phi_0 coupled)
+     R1 (-Q1 + Q2 + Q5)' + Q5/C2 + R3 (Q3 - Q4 + Q5)' = 0
+   discretised by BDF2 (App. A; the matrix and history terms are formed from
+   these equations).  The gap is the load capacitor C3, its electrode charge
+   Q_circ = Q4 (Sec. 2.4.2); strict coupling folds Q4 = K - [T'^{-1}]_44 phi_0
+   into the x = 0 row (Eqs. Q4_phi_relation, K_def, Poisson_BC2), weak
+   coupling advances the loops alone with C3's voltage starting from phi_0 of
+   the previous level.  Before t = 0 the circuit rests with only C1 charged,
+   to V1; the first step redistributes that charge around the capacitor loop
+   C1-C2-C3.  All values SI and > 0 except M >= 0 (M^2 < L1 L2). */
+typedef struct {
+  double R1, R2, R3;
+  double C1, C2, C3;
+  double L1, L2, M;
+  double V1; /* initial voltage of C1 [V] */
+} cp_tesla;
+
+/* External circuit (Sec. 2.1, App. A).  kind CP_CIRCUIT_SERIES_RLC: a series
+   R-L loop with the source V_s(t) = V0 (1 - cos 2 pi f t) exp(-t/tau) / 2
+   driving the x = 0 electrode with sign `polarity`; C is the load
+   capacitance used by the weak scheme's free circuit solve (Sec. 2.4.3) and
+   to derive A when area == 0.  kind CP_CIRCUIT_TESLA: `tesla` (R, L, C, V0,
+   f, tau and polarity unused; the load capacitance is tesla.C3). */
 typedef struct {
   double R, L, C;
   double V0, f, tau;
   double polarity;
   int32_t kind; /* CP_CIRCUIT_* */
   int32_t pad0;
+  cp_tesla tesla;
 } cp_circuit;
 
-/* Ion-induced SEE (Sec. 2.3) and the ion beam entering at x = d.
-   Mean yield gamma(E) = min(scale * gamma_coef * sqrt(E / E_ref), gamma_max),
-   count = floor(gamma) + Bernoulli(gamma - floor(gamma)), speed of each
-   emitted electron = sqrt(e T_emit / m_e) |N(0,1)|, normal emission.  Beam:
+/* Ion-induced SEE (Sec. 2.3, Algorithm see_sampling_1d) and the ion beam
+   entering at x = d.  Mean yield gamma(E) = min(scale * gamma_coef *
+   sqrt(E / E_ref), gamma_max) (the paper's fitted polynomial has no
+   published coefficients; this law stands in), 0 <= gamma_max <= 14.
+   Count: count_law CP_SEE_COUNT_BERNOULLI floor(gamma) + Bernoulli(gamma -
+   floor(gamma)), or CP_SEE_COUNT_POISSON Poisson(gamma) as in the paper,
+   sampled by inversion of its distribution function (at most 64 electrons).
+   Speed of each emitted electron: energy_law CP_SEE_ENERGY_MAXWELL
+   sqrt(e T_emit / m_e) |N(0,1)|, or CP_SEE_ENERGY_LOGNORMAL as in the paper:
+   energy E = exp(ln_mu + ln_sigma N(0,1)) eV, speed sqrt(2 E e / m_e) (the
+   paper's fitted mu, sigma are not published).  Normal emission.  Beam:
    beam_per_step ions per step, energy beam_E_eV (mode 0) or uniform in
-   [beam_Emin_eV, beam_Emax_eV] (mode 1).  0 <= gamma_max <= 14. */
+   [beam_Emin_eV, beam_Emax_eV] (mode 1). */
 typedef struct {
   double gamma_coef, gamma_max, E_ref_eV, scale, T_emit_eV;
   double beam_E_eV, beam_Emin_eV, beam_Emax_eV;
   int32_t beam_per_step;
   int32_t beam_mode;
+  int32_t count_law;  /* CP_SEE_COUNT_* */
+  int32_t energy_law; /* CP_SEE_ENERGY_* */
+  double ln_mu, ln_sigma; /* lognormal law: ln(E / 1 eV) ~ N(ln_mu, ln_sigma^2) */
 } cp_see_beam;
+
+#define CP_SEE_COUNT_BERNOULLI 0
+#define CP_SEE_COUNT_POISSON 1
+#define CP_SEE_ENERGY_MAXWELL 0
+#define CP_SEE_ENERGY_LOGNORMAL 1
 
 /* Run controls.  Capacities are per species in macroparticles (0 picks a
    default from the loaded counts and max_steps). */
@@ -283,7 +324,8 @@ int cp_read_launch_times(cp_ctx* ctx, double* ms, int64_t cap, int64_t* n);
    calls that overlap on the GPU (other streams, other host threads) race.
    Errors: CP_ERR_ARG (null buffer, n_cells outside 2..4096, bad sizes, a
    SEE law cp_create would refuse: gamma_max outside 0..14, a negative or
-   non-finite scale, gamma_coef, E_ref_eV or T_emit_eV),
+   non-finite scale, gamma_coef, E_ref_eV or T_emit_eV; a count or energy
+   law other than floor + Bernoulli and the half-Maxwellian),
    CP_ERR_CAPACITY (n > 524288 ions, the scratch's limit; or more emitted
    electrons than se_cap), CP_ERR_CUDA. */
 int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, double dt, uint64_t seed,

@@ -126,6 +126,88 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? CP_OK : CP_ERR_CUDA; }
 
 int64_t round4(int64_t n) { return (n + 3) & ~int64_t(3); }
 
+// --- Tesla transformer (Sec. 2.1, App. A): BDF2 of the loop equations ----
+// Matrix of the level-n terms; coupled: loop 4 without its 1/C3 (the load
+// capacitor's voltage is then phi_0, Sec. 2.4.2).
+void tesla_matrix(const cp_tesla& q, double dt, bool coupled, double T[5][5]) {
+  const double a = 3.0 / (2.0 * dt), b = 9.0 / (4.0 * dt * dt);
+  const double r1 = a * q.R1, r2 = a * q.R2, r3 = a * q.R3, m = b * q.M;
+  const double rows[5][5] = {
+      {1.0 / q.C1 + r1, -r1, 0.0, 0.0, -r1},
+      {-r1, r1 + r2 + b * q.L1, m, 0.0, r1},
+      {0.0, m, b * q.L2 + r3, -r3, r3},
+      {0.0, 0.0, -r3, r3 + (coupled ? 0.0 : 1.0 / q.C3), -r3},
+      {-r1, r1, r3, -r3, r1 + r3 + 1.0 / q.C2}};
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) T[i][j] = rows[i][j];
+}
+
+// History terms c = H h of the same equations, h[5 k + i] = Q_i of level n-1-k.
+void tesla_history(const cp_tesla& q, double dt, const double h[20], double c[5]) {
+  double h1[5], h2[5];
+  for (int i = 0; i < 5; ++i) {
+    h1[i] = (4.0 * h[i] - h[5 + i]) / (2.0 * dt);
+    h2[i] = (24.0 * h[i] - 22.0 * h[5 + i] + 8.0 * h[10 + i] - h[15 + i]) / (4.0 * dt * dt);
+  }
+  const double x1 = h1[0] - h1[1] - h1[4], x3 = h1[2] - h1[3] + h1[4];
+  c[0] = q.R1 * x1;
+  c[1] = -q.R1 * x1 + q.R2 * h1[1] + q.L1 * h2[1] + q.M * h2[2];
+  c[2] = q.M * h2[1] + q.L2 * h2[2] + q.R3 * x3;
+  c[3] = -q.R3 * x3;
+  c[4] = -q.R1 * x1 + q.R3 * x3;
+}
+
+// X = T^{-1} B for a 5 x m right-hand side (Gaussian elimination, partial pivoting).
+bool solve5(double T[5][5], double* B, int m) {
+  for (int k = 0; k < 5; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < 5; ++i)
+      if (std::fabs(T[i][k]) > std::fabs(T[piv][k])) piv = i;
+    if (!(std::fabs(T[piv][k]) > 0.0)) return false;
+    if (piv != k) {
+      for (int j = 0; j < 5; ++j) std::swap(T[k][j], T[piv][j]);
+      for (int j = 0; j < m; ++j) std::swap(B[k * m + j], B[piv * m + j]);
+    }
+    for (int i = k + 1; i < 5; ++i) {
+      const double f = T[i][k] / T[k][k];
+      for (int j = k; j < 5; ++j) T[i][j] -= f * T[k][j];
+      for (int j = 0; j < m; ++j) B[i * m + j] -= f * B[k * m + j];
+    }
+  }
+  for (int i = 4; i >= 0; --i)
+    for (int j = 0; j < m; ++j) {
+      double s = B[i * m + j];
+      for (int l = i + 1; l < 5; ++l) s -= T[i][l] * B[l * m + j];
+      B[i * m + j] = s / T[i][i];
+    }
+  return true;
+}
+
+// The linear maps of the strict and weak Tesla solves (cpk::DevParams t_*).
+bool tesla_setup(const cp_tesla& q, double dt, cpk::DevParams* P) {
+  double H[5 * 21];  // columns: H e_j (j < 20), then e4
+  for (int j = 0; j < 20; ++j) {
+    double h[20] = {0.0}, c[5];
+    h[j] = 1.0;
+    tesla_history(q, dt, h, c);
+    for (int i = 0; i < 5; ++i) H[i * 21 + j] = c[i];
+  }
+  for (int i = 0; i < 5; ++i) H[i * 21 + 20] = (i == 3) ? 1.0 : 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double T[5][5], X[5 * 21];
+    std::memcpy(X, H, sizeof(X));
+    tesla_matrix(q, dt, pass == 0, T);
+    if (!solve5(T, X, 21)) return false;
+    for (int i = 0; i < 5; ++i) {
+      for (int j = 0; j < 20; ++j) (pass == 0 ? P->t_Ps : P->t_Pw)[i][j] = X[i * 21 + j];
+      (pass == 0 ? P->t_ws : P->t_ww)[i] = X[i * 21 + 20];
+    }
+  }
+  for (int i = 0; i < 5; ++i) P->t_Q0[i] = 0.0;
+  P->t_Q0[0] = q.C1 * q.V1;
+  return true;
+}
+
 // macroparticle weight and the charge scales that follow from it
 void set_weight(cpk::DevParams* P, double w) {
   P->weight = w;
@@ -295,6 +377,8 @@ int initialize(cp_ctx* c, int mode, double tol) {
   S.id_alt = c->buf_id[1];
   S.sigma = c->sigma0;
   S.beam_id_base = id_base;
+  for (int k = 0; k < 4; ++k)  // the circuit rests before t = 0
+    for (int i = 0; i < 5; ++i) S.Qt[k][i] = c->hp.t_Q0[i];
   CP_TRY(alloc(reinterpret_cast<void**>(&c->dS), sizeof(cpk::DevState)));
   CP_CUDA(cudaMemcpyAsync(c->dS, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
   CP_CUDA(cudaStreamSynchronize(c->stream));
@@ -440,14 +524,28 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   if (gap->n_cells < 2 || !(gap->d > 0) || !(run->dt > 0) || !(gap->weight > 0) ||
       !(gap->eps0 > 0) || !(gap->e > 0) || !(gap->m_e > 0) || !(gap->m_i > 0) ||
       (run->precision != CP_FP64 && run->precision != CP_FP32) ||
-      (circ->kind != CP_CIRCUIT_SERIES_RLC && circ->kind != CP_CIRCUIT_OPEN) ||
+      (circ->kind != CP_CIRCUIT_SERIES_RLC && circ->kind != CP_CIRCUIT_OPEN &&
+       circ->kind != CP_CIRCUIT_TESLA) ||
       see->beam_per_step < 0 || (see->beam_mode != 0 && see->beam_mode != 1) || run->max_steps < 0 ||
-      !(see->gamma_max >= 0.0 && see->gamma_max <= 14.0))
+      !(see->gamma_max >= 0.0 && see->gamma_max <= 14.0) ||
+      (see->count_law != CP_SEE_COUNT_BERNOULLI && see->count_law != CP_SEE_COUNT_POISSON) ||
+      (see->energy_law != CP_SEE_ENERGY_MAXWELL && see->energy_law != CP_SEE_ENERGY_LOGNORMAL))
     return CP_ERR_ARG;
+  if (see->energy_law == CP_SEE_ENERGY_LOGNORMAL &&
+      (!std::isfinite(see->ln_mu) || !(see->ln_sigma >= 0.0) || !(see->ln_mu + 9.0 * see->ln_sigma < 600.0)))
+    return CP_ERR_ARG;  // exp(mu + sigma z) stays finite for |z| < 9 (|z| <= 8.6 from 52-bit draws)
   if (circ->kind == CP_CIRCUIT_SERIES_RLC && (!(circ->C > 0) || !(circ->R >= 0) || !(circ->L >= 0) ||
                                               !(circ->R > 0 || circ->L > 0) || !(circ->tau > 0)))
     return CP_ERR_ARG;
-  if (!(gap->area > 0) && !(circ->C > 0)) return CP_ERR_ARG;
+  if (circ->kind == CP_CIRCUIT_TESLA) {
+    const cp_tesla& q = circ->tesla;
+    const double pos[8] = {q.R1, q.R2, q.R3, q.C1, q.C2, q.C3, q.L1, q.L2};
+    for (double v : pos)
+      if (!(v > 0) || !std::isfinite(v)) return CP_ERR_ARG;
+    if (!(q.M >= 0) || !(q.M * q.M < q.L1 * q.L2) || !std::isfinite(q.V1)) return CP_ERR_ARG;
+  }
+  const double C_load = (circ->kind == CP_CIRCUIT_TESLA) ? circ->tesla.C3 : circ->C;
+  if (!(gap->area > 0) && !(C_load > 0)) return CP_ERR_ARG;
   cp_ctx* c = new (std::nothrow) cp_ctx();
   if (!c) return CP_ERR_OOM;
   int smem_optin = 0;
@@ -481,7 +579,7 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.d = gap->d;
   P.dx = gap->d / static_cast<double>(gap->n_cells);
   P.dt = run->dt;
-  P.area = gap->area > 0 ? gap->area : circ->C * gap->d / gap->eps0;
+  P.area = gap->area > 0 ? gap->area : C_load * gap->d / gap->eps0;
   P.eps0 = gap->eps0;
   P.e = gap->e;
   P.m_e = gap->m_e;
@@ -489,7 +587,7 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.weight = gap->weight;
   P.R = circ->R;
   P.L = circ->L;
-  P.C = circ->C;
+  P.C = C_load;
   P.V0 = circ->V0;
   P.f = circ->f;
   P.tau = circ->tau > 0 ? circ->tau : 1.0;
@@ -511,6 +609,11 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.kappa[CP_IONS] = P.e * dt * dt / (P.m_i * dx);
   P.kappa[CP_SECONDARIES] = P.kappa[CP_ELECTRONS];
   P.see_vth = std::sqrt(P.e * P.T_emit_eV / P.m_e);
+  P.see_count_law = see->count_law;
+  P.see_energy_law = see->energy_law;
+  P.see_ln_mu = see->ln_mu;
+  P.see_ln_sigma = see->ln_sigma;
+  P.see_v_eV = std::sqrt(2.0 * P.e / P.m_e);
   P.a21 = 9.0 * P.L / (4.0 * dt * dt) + 3.0 * P.R / (2.0 * dt);
   P.alpha = dx * dx * P.scale / P.eps0;
   P.g_strict = P.a21 > 0 ? 1.0 / P.a21 : 0.0;
@@ -531,6 +634,16 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
     P.kap_f[1][s] = static_cast<float>(P.kap_d[1][s]);
   }
   P.precision = run->precision;
+  if (circ->kind == CP_CIRCUIT_TESLA) {
+    if (!tesla_setup(circ->tesla, dt, &P)) {
+      cudaStreamDestroy(c->cap_stream);
+      delete c;
+      return CP_ERR_ARG;
+    }
+    P.gam_tesla = P.t_ws[3] * dx / (P.eps0 * P.area);
+    P.inv_den_tesla = 1.0 / (1.0 + static_cast<double>(P.N) * P.gam_tesla);
+    P.V0 = 0.0;  // no source: the circuit starts from the charged C1
+  }
   *out = c;
   return CP_OK;
 }
@@ -628,6 +741,11 @@ int cp_set_predictor(cp_ctx* c, const float* params, const cp_predictor* norm) {
   if (rc == CP_OK)
     rc = cuda_rc(cudaMemcpyAsync(&c->net->bound, &norm->bound, sizeof(double),
                                  cudaMemcpyHostToDevice, c->stream));
+  double inv[CP_PRED_FEATURES];
+  for (int f = 0; f < CP_PRED_FEATURES; ++f) inv[f] = 1.0 / static_cast<double>(norm->in_scale[f]);
+  if (rc == CP_OK)
+    rc = cuda_rc(cudaMemcpyAsync(c->net->inv_in_scale, inv, sizeof(inv), cudaMemcpyHostToDevice,
+                                 c->stream));
   if (rc == CP_OK) rc = cuda_rc(cudaStreamSynchronize(c->stream));
   cudaFree(dparams);
   // graphs captured before carry the old buffer set: rebuild on next use
@@ -1532,6 +1650,8 @@ int g2_init(cp_gap2d* g, int mode, double tol) {
   S.id_alt = c->buf_id[1];
   S.sigma = c->sigma0;
   S.beam_id_base = id_base;
+  for (int k = 0; k < 4; ++k)  // the circuit rests before t = 0
+    for (int i = 0; i < 5; ++i) S.Qt[k][i] = c->hp.t_Q0[i];
   CP_TRY(alloc(reinterpret_cast<void**>(&c->dS), sizeof(cpk::DevState)));
   CP_CUDA(cudaMemcpyAsync(c->dS, &S, sizeof(S), cudaMemcpyHostToDevice, c->stream));
   // 2D grids and tables

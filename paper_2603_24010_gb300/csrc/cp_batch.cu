@@ -311,13 +311,9 @@ k_push_ens(const Bufs* __restrict__ Ball, int E, int n_max, AbsRecE* __restrict_
                   static_cast<unsigned long long>(nse));
     real* xs = reinterpret_cast<real*>(Si->xi[CP_SECONDARIES]);
     real* us = reinterpret_cast<real*>(Si->u[CP_SECONDARIES]);
-    const double pi = 3.14159265358979323846;
     for (int jn = 0; jn < nse; ++jn) {
-      const U64x4 wv = philox4x64_10(rec.id, static_cast<uint64_t>(step), static_cast<uint64_t>(1 + jn),
-                                     0, Pi->seed, kTagSee);
-      const double ua = u01(wv.w[0]), ub = u01(wv.w[1]), frac = u01(wv.w[2]);
-      const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
-      const double vse = Pi->see_vth * fabs(z);
+      double frac;
+      const double vse = see_speed(Pi, rec.id, step, jn, &frac);
       const double use = vse * dt / dx;
       const double xd = (el == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(Ni), __dmul_rn(use, frac));
       const real xr = nudge_inside<real>(xd, Ni);

@@ -114,8 +114,39 @@ __device__ __forceinline__ int see_count(const DevParams* P, double Eev, uint64_
   if (!(g > 0.0)) g = 0.0;
   const U64x4 w = philox4x64_10(id, static_cast<uint64_t>(step), 0, 0, P->seed, kTagSee);
   const double u1 = u01(w.w[0]);
+  if (P->see_count_law == CP_SEE_COUNT_POISSON) {
+    // Poisson(gamma) (Algorithm see_sampling_1d) by inversion: the smallest n
+    // whose cumulative probability exceeds u1, at most kSeePoissonMax
+    double pk = exp(-g), F = pk;
+    int n = 0;
+    while (u1 >= F && n < kSeePoissonMax) {
+      n += 1;
+      pk = __ddiv_rn(__dmul_rn(pk, g), static_cast<double>(n));
+      F = __dadd_rn(F, pk);
+    }
+    return n;
+  }
   const double fl = floor(g);
   return static_cast<int>(fl) + ((u1 < __dsub_rn(g, fl)) ? 1 : 0);
+}
+
+// Speed [m/s] of emitted electron j of an impact and the fraction of the step
+// it has flown (draws 0, 1: Box-Muller normal z; draw 2: the fraction) of
+// counter (id, step, 1 + j): |z| sqrt(e T_emit / m_e) (half-Maxwellian), or
+// the lognormal law of Algorithm see_sampling_1d, E = exp(mu + sigma z) eV.
+__device__ __forceinline__ double see_speed(const DevParams* P, uint64_t id, int64_t step, int j,
+                                            double* frac) {
+  const double pi = 3.14159265358979323846;
+  const U64x4 wv = philox4x64_10(id, static_cast<uint64_t>(step), static_cast<uint64_t>(1 + j), 0,
+                                 P->seed, kTagSee);
+  const double ua = u01(wv.w[0]), ub = u01(wv.w[1]);
+  *frac = u01(wv.w[2]);
+  const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
+  if (P->see_energy_law == CP_SEE_ENERGY_LOGNORMAL) {
+    const double E_eV = exp(__dadd_rn(P->see_ln_mu, __dmul_rn(P->see_ln_sigma, z)));
+    return sqrt(__ddiv_rn(__dmul_rn(__dmul_rn(2.0, E_eV), P->e), P->m_e));
+  }
+  return P->see_vth * fabs(z);
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

@@ -49,6 +49,7 @@ constexpr int kPredIn = kPredWindow * kPredFeat;  // 40
 constexpr int kHid = 64;
 constexpr int kPredOut = 2;
 constexpr int kPredMinEval = 16;  // checked predictions before the first use
+constexpr int kSeePoissonMax = 64;  // truncation of the Poisson emission count
 constexpr double kPredAvg = 1.0 / 16.0;  // weight of the running error averages
 
 struct DevParams {
@@ -65,6 +66,9 @@ struct DevParams {
   double scale;          // rho_i = G_i * scale  [C/m^3]
   double kappa[kSpecies];  // q dt^2 / (m dx): cells/step^2 per V/m
   double see_vth;        // sqrt(e T_emit / m_e)
+  double see_ln_mu, see_ln_sigma;  // lognormal SE energy law: ln(E / 1 eV) ~ N(mu, sigma^2)
+  double see_v_eV;       // sqrt(2 e / m_e): speed of an electron of 1 eV
+  int32_t see_count_law, see_energy_law;
   double a21;            // 9 L / (4 dt^2) + 3 R / (2 dt): BDF2 coefficient of Q^n
   double alpha;          // dx^2 * scale / eps0: b_i = -alpha G_i
   // host-precomputed factors so that the solve divides nothing in FP64
@@ -76,6 +80,15 @@ struct DevParams {
   double dx_eps0;        // dx / eps0
   double inv_A, inv_dx, inv_2dt;
   double L4dt2, R2dt;    // L / (4 dt^2), R / (2 dt)
+  // Tesla transformer circuit: the new level's loop charges are linear in
+  // the 20 history values h (loop charges of levels n-1..n-4):
+  //   strict: Q^n = t_Ps h - phi_0 t_ws   (T'^{-1} H and T'^{-1} e4)
+  //   weak:   Q^n = t_Pw h + s t_ww       (T^{-1} H and T^{-1} e4, s the
+  //           capacitor term of loop 4)
+  double t_Ps[5][20], t_ws[5], t_Pw[5][20], t_ww[5];
+  double t_Q0[5];        // loop charges before t = 0
+  double gam_tesla;      // [T'^{-1}]_44 dx / (eps0 A)
+  double inv_den_tesla;  // 1 / (1 + N gam_tesla)
   float kap_f[2][kSpecies];   // kick factors in FP32: [0] half kick, [1] full kick
   double kap_d[2][kSpecies];  // the same in FP64
   int64_t cap[kSpecies];
@@ -102,6 +115,7 @@ struct DevState {
   int32_t status;        // 0 or a CP_ERR_* code; stepping stops while non-zero
   double sigma;          // sigma_+ at the current level
   double Qh[4];          // Q^{n}, Q^{n-1}, Q^{n-2}, Q^{n-3}
+  double Qt[4][5];       // Tesla circuit: loop charges of levels n, n-1, n-2, n-3
   int64_t n_alloc[kSpecies];  // slots in use (dead included); appends reserve here
   int64_t n_proc[kSpecies];   // slots processed by the current push (multiple of 4)
   int64_t n_live[kSpecies];
@@ -139,6 +153,7 @@ struct PredNet {
   float in_scale[kPredFeat];
   float out_scale[kPredOut];
   double bound;
+  double inv_in_scale[kPredFeat];  // 1 / in_scale, formed on the host
 };
 // bytes of a PredNet as allocated and copied (whole 16-byte chunks)
 constexpr size_t kPredNetBytes = (sizeof(PredNet) + 15) & ~size_t(15);

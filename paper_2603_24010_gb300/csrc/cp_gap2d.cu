@@ -384,13 +384,9 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
     float* us = reinterpret_cast<float*>(S->u[CP_SECONDARIES]);
     float* ys = reinterpret_cast<float*>(D.y[CP_SECONDARIES]);
     float* ws = reinterpret_cast<float*>(D.w[CP_SECONDARIES]);
-    const double pi = 3.14159265358979323846;
     for (int jn = 0; jn < nse; ++jn) {
-      const U64x4 wv = philox4x64_10(rec.id, static_cast<uint64_t>(step), static_cast<uint64_t>(1 + jn),
-                                     0, P->seed, kTagSee);
-      const double ua = u01(wv.w[0]), ub = u01(wv.w[1]), frac = u01(wv.w[2]);
-      const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
-      const double use = P->see_vth * fabs(z) * dt / dx;
+      double frac;
+      const double use = see_speed(P, rec.id, step, jn, &frac) * dt / dx;
       const double xd = (el == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(D.Nx), __dmul_rn(use, frac));
       const float xr = nudge_inside<float>(xd, D.Nx);
       const unsigned long long slot = wb + static_cast<unsigned long long>(jn);

@@ -260,7 +260,8 @@ extern "C" int cp_push_ions_noalloc(const cp_gap* gap, const cp_see_beam* see, d
   if (!(see->gamma_max >= 0.0 && see->gamma_max <= 14.0) || !(see->scale >= 0.0) ||
       !std::isfinite(see->scale) || !(see->gamma_coef >= 0.0) || !std::isfinite(see->gamma_coef) ||
       !(see->T_emit_eV >= 0.0) || !std::isfinite(see->T_emit_eV) || !(see->E_ref_eV >= 0.0) ||
-      !std::isfinite(see->E_ref_eV))
+      !std::isfinite(see->E_ref_eV) || see->count_law != CP_SEE_COUNT_BERNOULLI ||
+      see->energy_law != CP_SEE_ENERGY_MAXWELL)
     return CP_ERR_ARG;
   if (gap->n_cells < 2 || gap->n_cells > kMaxCells) return CP_ERR_ARG;  // shared-memory grid limit
   if (n > kMaxIons) return CP_ERR_CAPACITY;  // beyond the scratch array: every ion might be absorbed

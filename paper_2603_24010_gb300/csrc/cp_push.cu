@@ -206,13 +206,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push(Bufs B, int do_pu
       if (act && nse > 0) {
         real* xs = reinterpret_cast<real*>(S->xi[CP_SECONDARIES]);
         real* us = reinterpret_cast<real*>(S->u[CP_SECONDARIES]);
-        const double pi = 3.14159265358979323846;
         for (int j = 0; j < nse; ++j) {
-          const U64x4 wv = philox4x64_10(rec.id, static_cast<uint64_t>(step),
-                                         static_cast<uint64_t>(1 + j), 0, P->seed, kTagSee);
-          const double ua = u01(wv.w[0]), ub = u01(wv.w[1]), frac = u01(wv.w[2]);
-          const double z = sqrt(-2.0 * log(ua)) * cos(2.0 * pi * ub);  // Box-Muller
-          const double vse = P->see_vth * fabs(z);
+          double frac;
+          const double vse = see_speed(P, rec.id, step, j, &frac);
           const double use = vse * dt / dx;
           const double xd = (rec.electrode == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(N), __dmul_rn(use, frac));
           const real xr = nudge_inside<real>(xd, N);
@@ -227,9 +223,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push(Bufs B, int do_pu
           }
         }
       }
+      if (P->see_count_law == CP_SEE_COUNT_POISSON) {  // up to 512 x 64 electrons per round
+        __syncthreads();
+        fold(A, Bc, Gs, N, -1LL);
+        __syncthreads();
+      }
     }
     __syncthreads();
-    if (na > 0) {  // at most 4096 impacts x (floor(gamma_max) + 1) electrons: no 32-bit overflow
+    if (na > 0) {  // floor + Bernoulli: at most 4096 impacts x 15 electrons, no 32-bit overflow
       fold(A, Bc, Gs, N, -1LL);
       __syncthreads();
     }

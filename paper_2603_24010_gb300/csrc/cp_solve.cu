@@ -278,15 +278,16 @@ __device__ void cta_max3(unsigned long long& a, unsigned long long& b, unsigned 
 
 // Circuit charge, surface charge and current of a solved level from the
 // circuit scalars of the solve (sc: [2] g, [3] K or Q^n, [6] Q_conv, [7]
-// sigma_{n-1}, [8] Q^{n-1}, [9] Q^{n-2}) and the level's phi_0.
-__device__ __forceinline__ void level_charges(const DevParams* P, const double* sc, bool strict_rlc,
+// sigma_{n-1}, [8] Q^{n-1}, [9] Q^{n-2}) and the level's phi_0.  strict: a
+// circuit whose charge follows Q^n = K - g phi_0^n (series RLC or Tesla).
+__device__ __forceinline__ void level_charges(const DevParams* P, const double* sc, bool strict,
                                               double phi0, double* Qn, double* sigma_n, double* I) {
   const double Qconv = sc[6], sigma_prev = sc[7], Q1 = sc[8], Q2 = sc[9];
-  if (strict_rlc) {
+  if (strict) {
     *Qn = sc[3] - sc[2] * phi0;                             // Eqs. Q4_phi_relation, K_def
     *sigma_n = sigma_prev + (Qconv + *Qn - Q1) * P->inv_A;  // Eq. sigma_update
     *I = (3.0 * *Qn - 4.0 * Q1 + Q2) * P->inv_2dt;
-  } else if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
+  } else if (P->circuit != CP_CIRCUIT_OPEN) {
     *Qn = sc[3];                                            // weak: the circuit's loop charge
     *sigma_n = sigma_prev + (Qconv + *Qn - Q1) * P->inv_A;  // Eq. top_plate_charge
     *I = (3.0 * *Qn - 4.0 * Q1 + Q2) * P->inv_2dt;
@@ -323,7 +324,14 @@ __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, c
   __shared__ float h1[kHid], h2[kHid], h3[kHid];
   __shared__ float y[kPredOut];
   __shared__ double s_row[kPredFeat];
-  __shared__ int s_full, s_old;
+  __shared__ int s_full;
+  // the 7 older rows of the window (ring slots pos+1..pos+7, oldest first),
+  // loaded while thread 0 forms the new row
+  const int pos0 = static_cast<int>(sc[37]);
+  double v_old = 0.0;
+  if (threadIdx.x < kPredIn - kPredFeat)
+    v_old = S->feat[(pos0 + 1 + static_cast<int>(threadIdx.x) / kPredFeat) & (kPredWindow - 1)]
+                   [threadIdx.x % kPredFeat];
   if (threadIdx.x == 0) {
     double Qn, sigma_n, I;
     level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
@@ -334,16 +342,24 @@ __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, c
     row[2] = sigma_n * A - sc[7] * A;  // Q_surf^n - Q_surf^{n-1}
     row[3] = sc[33];                   // secondaries emitted at x = 0
     row[4] = sc[34];                   // energy of the ions absorbed at x = 0 [eV]
-    const int pos = S->feat_pos;
+    // the network's prediction for this level against the realised
+    // J^n = C (phi_0^n - phi_0^{n-1}) - (Q^n - Q^{n-1}) (running averages
+    // loaded with the circuit state at the solve's start)
+    if (sc[31] != 0.0) {
+      const double J = P->C * (phi0 - sc[32]) - (Qn - sc[8]);
+      S->err_avg = sc[45] + (fabs(J - sc[30]) - sc[45]) * kPredAvg;
+      S->J_avg = sc[46] + (fabs(J) - sc[46]) * kPredAvg;
+      S->n_eval = static_cast<long long>(sc[47]) + 1;
+    }
+    const int pos = static_cast<int>(sc[37]);  // read with the circuit state at the solve's start
     for (int f = 0; f < kPredFeat; ++f) {
       S->feat[pos][f] = row[f];
       s_row[f] = row[f];
     }
     S->feat_pos = (pos + 1) & (kPredWindow - 1);
-    const int nf = min(S->n_feat + 1, kPredWindow);
+    const int nf = min(static_cast<int>(sc[38]) + 1, kPredWindow);
     S->n_feat = nf;
     s_full = (nf == kPredWindow);
-    s_old = (pos + 1) & (kPredWindow - 1);  // ring slot of the oldest row
   }
   asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies of the network
   __syncthreads();
@@ -353,8 +369,8 @@ __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, c
   }
   if (threadIdx.x < kPredIn) {  // window position j (0 = oldest), feature f
     const int j = threadIdx.x / kPredFeat, f = threadIdx.x % kPredFeat;
-    const double v = (j == kPredWindow - 1) ? s_row[f] : S->feat[(s_old + j) & (kPredWindow - 1)][f];
-    x[threadIdx.x] = static_cast<float>(v / static_cast<double>(s_net->in_scale[f]));
+    const double v = (j == kPredWindow - 1) ? s_row[f] : v_old;
+    x[threadIdx.x] = static_cast<float>(v * s_net->inv_in_scale[f]);
   }
   __syncthreads();
   dense_one<kPredIn, kHid, true>(s_net->W1, s_net->b1, x, h1);
@@ -393,7 +409,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   __shared__ SolveSlotB slotB;
   __shared__ SolveSlotC slotC;
   __shared__ double slotd;
-  __shared__ double sc[40];
+  __shared__ double sc[48];
   __shared__ unsigned long long tal[11];  // the push's tallies, read early
   __shared__ int s_stop;
   __shared__ __align__(16) PredNet s_net;  // the network, for the CTA that runs it
@@ -438,6 +454,21 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   // source, the BDF2 history, the circuit solve and the x = 0 row's
   // right-hand side need no scan, so one thread of the last warp does them
   // -- and reads the push's tallies for the commit -- while the CTA scans.
+  // Tesla circuit: the last warp forms the new level's loop charges for
+  // phi_0 = 0 from the 20 history values (one per lane, warp sums)
+  double tq[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (P->circuit == CP_CIRCUIT_TESLA && do_push && threadIdx.x >= kSolveThreads - 32) {
+    const int l = static_cast<int>(lane_id());
+    const double h = (l < 20) ? ldcg(&S->Qt[l / 5][l % 5]) : 0.0;  // levels n-1..n-4
+    const double(*Pm)[20] = (mode == 0) ? P->t_Ps : P->t_Pw;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      double v = (l < 20) ? Pm[i][l] * h : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      tq[i] = v;
+    }
+  }
   if (threadIdx.x == kSolveThreads - 32) {
     const double qw = P->e * P->weight;
     const long long conv = do_push ? ldcg(&S->conv_count) : 0LL;
@@ -457,12 +488,23 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     const double phi0_prev = ldcg(&S->phi0_last);
     // learned weak scheme: the network's prediction of the plasma's change of
     // C phi_0 over this step, used while its tracked error is within bound
-    const int pred_ready = (B.net != nullptr) ? ldcg(&S->pred_ready) : 0;
-    const double J_pred = pred_ready ? ldcg(&S->J_pred) : 0.0;
-    double J_used = 0.0;
-    if (mode == 2 && pred_ready && ldcg(&S->n_eval) >= kPredMinEval &&
-        ldcg(&S->err_avg) <= B.net->bound * ldcg(&S->J_avg))
-      J_used = J_pred;
+    // (the predictor state is loaded in one batch: no chain of dependent loads)
+    int pred_ready = 0, feat_pos = 0, n_feat = 0;
+    long long n_eval = 0;
+    double J_pred = 0.0, err_avg = 0.0, J_avg = 0.0, bound = 0.0;
+    if (B.net != nullptr) {
+      pred_ready = ldcg(&S->pred_ready);
+      J_pred = ldcg(&S->J_pred);
+      n_eval = ldcg(&S->n_eval);
+      err_avg = ldcg(&S->err_avg);
+      J_avg = ldcg(&S->J_avg);
+      bound = B.net->bound;
+      feat_pos = ldcg(&S->feat_pos);
+      n_feat = ldcg(&S->n_feat);
+    }
+    if (!pred_ready) J_pred = 0.0;
+    const double J_used =
+        (mode == 2 && pred_ready && n_eval >= kPredMinEval && err_avg <= bound * J_avg) ? J_pred : 0.0;
     double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
     if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
       if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
@@ -475,6 +517,21 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
         // from phi_0^{n-1}: a21 Q - hist + phi_0^{n-1} + (Q - Q^{n-1} + J)/C = V_s
         Qpart = (Vs + hist + (Q1 - J_used) * P->inv_C - phi0_prev) * P->g_weak;
       }
+    } else if (P->circuit == CP_CIRCUIT_TESLA) {
+      // Q1 here is the load capacitor's loop charge Q4^{n-1}
+      if (!do_push) {  // level 0: the circuit as it rests before t = 0
+        Qpart = Q1;
+      } else if (mode == 0) {  // strict: Q4^n = K - [T'^{-1}]_44 phi_0^n
+        g = P->t_ws[3];
+        Qpart = tq[3];
+        gam = P->gam_tesla;
+        inv_den = P->inv_den_tesla;
+      } else {  // weak: loop 4's capacitor voltage phi_0^{n-1} + (Q4 - Q4^{n-1} + J)/C3
+        const double s = (Q1 - J_used) * P->inv_C - phi0_prev;
+        Qpart = tq[3] + s * P->t_ww[3];
+        sc[36] = s;
+      }
+      for (int i = 0; i < 5; ++i) sc[40 + i] = tq[i];
     }
     const double Qconv = static_cast<double>(conv) * qw;
     const double sigma_prev = ldcg(&S->sigma);
@@ -490,6 +547,11 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     sc[31] = static_cast<double>(pred_ready);
     sc[32] = phi0_prev;
     sc[35] = inv_den;
+    sc[37] = static_cast<double>(feat_pos);  // the predictor's ring slot for this level
+    sc[38] = static_cast<double>(n_feat);
+    sc[45] = err_avg;  // the predictor's running error averages, updated by its CTA
+    sc[46] = J_avg;
+    sc[47] = static_cast<double>(n_eval);
     if (do_push) {  // the push's tallies, read before the commit clears them
       sc[33] = static_cast<double>(ldcg(&S->emitted[0]));
       sc[34] = static_cast<double>(ldcg(&S->ion_energy_q)) / 256.0;
@@ -601,6 +663,8 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   __syncthreads();
 
   const bool strict_rlc = (P->circuit == CP_CIRCUIT_SERIES_RLC && mode == 0);
+  // the level's charge follows Q^n = K - g phi_0^n (g = 0 at a Tesla level 0)
+  const bool strict_c = (P->circuit != CP_CIRCUIT_OPEN) && (mode == 0 || (P->circuit == CP_CIRCUIT_TESLA && !do_push));
   // The neighbouring chunks' edge values follow from the exact prefixes with
   // the same arithmetic their owners use, so no exchange is needed:
   // x_{lo-1} needs P_{lo-1} = P_lo - S'_{lo-1}; x_hi needs P_hi; E_hi needs S'_hi.
@@ -749,7 +813,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   // rank's remote reads are done
   cl.barrier_wait(std::move(done_tok));
   if (rank == 1) {  // the predictor runs beside rank 0's commit
-    if (runs_net) predictor_update(B.P, B.S, &s_net, sc, strict_rlc, phi0_fin);
+    if (runs_net) predictor_update(B.P, B.S, &s_net, sc, strict_c, phi0_fin);
     return;
   }
   if (rank != 0) return;
@@ -761,7 +825,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     const double Qconv = sc[6], Q1 = sc[8], Q2 = sc[9], Q3 = sc[10];
     const long long conv = static_cast<long long>(sc[12]);
     double Qn, sigma_n, I;
-    level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
+    level_charges(P, sc, strict_c, phi0, &Qn, &sigma_n, &I);
     int status = 0;
     if (!isfinite(phi0) || !isfinite(sigma_n) || !isfinite(Qn)) status = CP_ERR_NONFINITE;
     else if (eta > tol) status = CP_ERR_RESIDUAL;
@@ -794,15 +858,17 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     S->cur = d;
     if (level < B.hist_rows) B.hist[level] = d;
 
-    // the network's prediction for this level against the realised
-    // J^n = C (phi_0^n - phi_0^{n-1}) - (Q^n - Q^{n-1})
-    if (sc[31] != 0.0) {
-      const double J = P->C * (phi0 - sc[32]) - (Qn - Q1);
-      S->err_avg += (fabs(J - sc[30]) - S->err_avg) * kPredAvg;
-      S->J_avg += (fabs(J) - S->J_avg) * kPredAvg;
-      S->n_eval += 1;
-    }
     // commit the circuit and surface-charge state of the new level
+    if (P->circuit == CP_CIRCUIT_TESLA && do_push) {  // the five loop charges
+      double Qv[5];
+      for (int i = 0; i < 5; ++i)
+        Qv[i] = (mode == 0) ? sc[40 + i] - phi0 * P->t_ws[i] : sc[40 + i] + sc[36] * P->t_ww[i];
+      for (int k = 3; k > 0; --k)
+        for (int i = 0; i < 5; ++i) S->Qt[k][i] = S->Qt[k - 1][i];
+      for (int i = 0; i < 5; ++i) S->Qt[0][i] = Qv[i];
+      if (!isfinite(Qv[0]) || !isfinite(Qv[1]) || !isfinite(Qv[2]) || !isfinite(Qv[4]))
+        status = CP_ERR_NONFINITE;
+    }
     S->sigma = sigma_n;
     S->phi0_last = phi0;
     S->Qh[3] = Q3;
@@ -843,7 +909,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   }
   if (nr == 1 && runs_net) {  // a one-CTA solve runs the predictor itself
     __syncthreads();
-    predictor_update(B.P, B.S, &s_net, sc, strict_rlc, phi0_fin);
+    predictor_update(B.P, B.S, &s_net, sc, strict_c, phi0_fin);
   }
 }
 

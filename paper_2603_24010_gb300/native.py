@@ -17,7 +17,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_RESIDUAL, ERR_NONFINITE, ERR_T
     0, -1, -2, -3, -4, -5, -6, -7)
 ELECTRONS, IONS, SECONDARIES = 0, 1, 2
 FP64, FP32 = 0, 1
-SERIES_RLC, OPEN = 0, 1
+SERIES_RLC, OPEN, TESLA = 0, 1, 2
 UNITS_CELL, UNITS_SI = 0, 1
 
 #: every symbol ``include/cp.h`` declares
@@ -55,16 +55,22 @@ class cp_gap(C.Structure):
                                           "sigma0")] + [("n_cells", C.c_int32), ("pad0", C.c_int32)]
 
 
+class cp_tesla(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("R1", "R2", "R3", "C1", "C2", "C3", "L1", "L2", "M",
+                                          "V1")]
+
+
 class cp_circuit(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("R", "L", "C", "V0", "f", "tau", "polarity")] + [
-        ("kind", C.c_int32), ("pad0", C.c_int32)]
+        ("kind", C.c_int32), ("pad0", C.c_int32), ("tesla", cp_tesla)]
 
 
 class cp_see_beam(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("gamma_coef", "gamma_max", "E_ref_eV", "scale",
                                           "T_emit_eV", "beam_E_eV", "beam_Emin_eV",
                                           "beam_Emax_eV")] + [
-        ("beam_per_step", C.c_int32), ("beam_mode", C.c_int32)]
+        ("beam_per_step", C.c_int32), ("beam_mode", C.c_int32), ("count_law", C.c_int32),
+        ("energy_law", C.c_int32), ("ln_mu", C.c_double), ("ln_sigma", C.c_double)]
 
 
 class cp_species(C.Structure):
@@ -393,11 +399,15 @@ def structs_from_config(cfg, capacity=(0, 0, 0), max_steps=None, compact_every=0
                  sigma0=cfg.get("sigma0", 0.0), n_cells=int(cfg["n_cells"]))
     circ = cp_circuit(R=cfg["R"], L=cfg["L"], C=cfg["C"], V0=cfg["V0"], f=cfg["f"],
                       tau=cfg["tau"], polarity=cfg["polarity"], kind=int(cfg.get("circuit", 0)))
+    if circ.kind == TESLA:
+        circ.tesla = cp_tesla(**{k: cfg["t" + k] for k, _ in cp_tesla._fields_})
     see = cp_see_beam(gamma_coef=cfg["gamma_coef"], gamma_max=cfg["gamma_max"],
                       E_ref_eV=cfg["E_ref_eV"], scale=cfg["see_scale"], T_emit_eV=cfg["T_emit_eV"],
                       beam_E_eV=cfg["beam_E_eV"], beam_Emin_eV=cfg["beam_Emin_eV"],
                       beam_Emax_eV=cfg["beam_Emax_eV"], beam_per_step=int(cfg["beam_per_step"]),
-                      beam_mode=int(cfg["beam_mode"]))
+                      beam_mode=int(cfg["beam_mode"]), count_law=int(cfg.get("see_count_law", 0)),
+                      energy_law=int(cfg.get("see_energy_law", 0)),
+                      ln_mu=float(cfg.get("see_ln_mu", 0.0)), ln_sigma=float(cfg.get("see_ln_sigma", 0.0)))
     run = cp_run(dt=cfg["dt"], seed=int(cfg["seed"]), max_steps=int(max_steps or cfg["steps"]),
                  precision=int(cfg.get("precision", FP64)), compact_every=int(compact_every))
     for s in range(3):

@@ -93,14 +93,15 @@ def ensemble_strict_samples(cfgs, steps=None, capacity=(0, 0, 0)):
 def ensemble_evaluate(cfgs, params, norm, steps=None, capacity=(0, 0, 0),
                       modes=(native.STRICT, native.WEAK, native.WEAK_LEARNED)):
     """Every run under each scheme, as one ensemble per scheme (the network
-    installed on every instance); V_gap(t) and J_hat histories (runs x
+    installed on every instance of the learned scheme only, so that the
+    other schemes run without it); V_gap(t) and J_hat histories (runs x
     levels) and the ensemble's wall time per step."""
     torch = _torch()
     steps = int(steps or cfgs[0]["steps"])
     out = {}
     for mode in modes:
         b = load_batch(cfgs, steps, capacity)
-        if params is not None:
+        if params is not None and mode == native.WEAK_LEARNED:
             for i in range(len(cfgs)):
                 b.set_predictor(i, params, norm)
         _step_batch(b, mode, 1)  # level 0 solve and first push outside the timing
@@ -174,13 +175,14 @@ def train(X, Y, iters=3000, batch=8192, lr=2e-3, lr_final=1e-4, seed=0, bound=0.
 
 def evaluate(cfg, params, norm, steps=None, modes=(native.STRICT, native.WEAK,
                                                     native.WEAK_LEARNED)):
-    """Run the same instance under each scheme; V_gap(t) histories and timings."""
+    """Run the same instance under each scheme (the network installed for the
+    learned scheme only); V_gap(t) histories and timings."""
     torch = _torch()
     steps = int(steps or cfg["steps"])
     out = {}
     for mode in modes:
         g = load_gap(cfg, steps)
-        if params is not None:
+        if params is not None and mode == native.WEAK_LEARNED:
             g.set_predictor(params, norm)
         g.step(mode, 1)  # level 0 solve and first push outside the timing
         torch.cuda.synchronize()
