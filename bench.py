@@ -250,10 +250,14 @@ def run_native(args, rank, world):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_window:  # a profiler started with profiling off captures the timed steps only
+        torch.cuda.profiler.start()
     e0.record(stream)
     g.step(0, K)
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_window:
+        torch.cuda.profiler.stop()
     barrier()
     ms = e0.elapsed_time(e1)
     launches = native.cp_last_launch_count(g.ctx)
@@ -663,6 +667,9 @@ def main():
                     help="override the workload's loaded pairs (weight scaled to keep the density)")
     ap.add_argument("--single", action="store_true",
                     help="only the device-resident graph pass (for profiler captures)")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for a profiler "
+                         "run with --profile-from-start off)")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the learned-vs-plain weak coupling comparison")
     ap.add_argument("--coupling-train", type=int, default=2048)

@@ -229,6 +229,9 @@ cpk::Bufs make_bufs(const cp_ctx* c) {
   B.hist_rows = c->hist_rows;
   B.vs = c->vs;
   B.net = c->net;
+  // a single FP32 gap evaluates the predictor in the next push's idle tail;
+  // ensemble members and the 2D gap's mean keep it in the solve
+  B.net_in_push = (c->precision == CP_FP32 && !c->ens_member) ? 1 : 0;
   return B;
 }
 
@@ -602,6 +605,12 @@ int cp_create(const cp_gap* gap, const cp_circuit* circ, const cp_see_beam* see,
   P.beam_Emax_eV = see->beam_Emax_eV;
   // the oracle's order of operations: (sqrt((2 E) e / m_i) dt) / dx, each rounded
   P.beam_ub = std::sqrt(2.0 * P.beam_E_eV * gap->e / gap->m_i) * run->dt / (gap->d / gap->n_cells);
+  {  // uniform beam in the FP32 pushes: (sqrt(2 E e / m_i) dt / dx)^2 = E k, linear in the draw
+    const double r = run->dt / (gap->d / gap->n_cells);
+    const double k = 2.0 * gap->e / gap->m_i * r * r;
+    P.beam_c0 = P.beam_Emin_eV * k;
+    P.beam_c1 = (P.beam_Emax_eV - P.beam_Emin_eV) * k;
+  }
   P.seed = run->seed;
   P.scale = P.e * P.weight / (P.area * P.dx * cpk::kFix);
   const double dt = P.dt, dx = P.dx;

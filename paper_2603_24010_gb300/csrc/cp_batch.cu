@@ -356,11 +356,16 @@ k_push_ens(const Bufs* __restrict__ Ball, int E, int n_max, AbsRecE* __restrict_
         const U64x4 wv = philox4x64_10(static_cast<uint64_t>(k), static_cast<uint64_t>(step), 0, 0,
                                        Pi->seed, kTagBeam);
         const double frac = u01(wv.w[0]);
-        const double Eb = (Pi->beam_mode == 0)
-                              ? Pi->beam_E_eV
-                              : __dadd_rn(Pi->beam_Emin_eV, __dmul_rn(__dsub_rn(Pi->beam_Emax_eV, Pi->beam_Emin_eV), u01(wv.w[1])));
-        const double v = sqrt(2.0 * Eb * Pi->e / Pi->m_i);
-        const double ub = v * dt / dx;
+        double ub;
+        if constexpr (sizeof(real) == 4) {  // the single FP32 gap's arithmetic
+          ub = beam_speed_fp32(Pi, u01(wv.w[1]));
+        } else {  // the single FP64 gap's: the definition's order of operations
+          const double Eb = (Pi->beam_mode == 0)
+                                ? Pi->beam_E_eV
+                                : __dadd_rn(Pi->beam_Emin_eV, __dmul_rn(__dsub_rn(Pi->beam_Emax_eV, Pi->beam_Emin_eV), u01(wv.w[1])));
+          const double v = sqrt(2.0 * Eb * Pi->e / Pi->m_i);
+          ub = v * dt / dx;
+        }
         const real xr = nudge_inside<real>(__dsub_rn(static_cast<double>(Ni), __dmul_rn(ub, frac)), Ni);
         const unsigned long long slot =
             wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));

@@ -149,6 +149,15 @@ __device__ __forceinline__ double see_speed(const DevParams* P, uint64_t id, int
   return P->see_vth * fabs(z);
 }
 
+// Entry speed [cells/step] of a beam ion in the FP32 pushes (Sec. 3.2): the
+// mono-energetic speed formed on the host, or sqrt(2 E e / m_i) dt / dx for
+// E = E_min + (E_max - E_min) u written as sqrt(c0 + c1 u) (one FMA and one
+// square root in FP64; the result is stored in FP32).
+__device__ __forceinline__ double beam_speed_fp32(const DevParams* P, double u) {
+  if (P->beam_mode == 0) return P->beam_ub;
+  return sqrt(fma(u, P->beam_c1, P->beam_c0));
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 __device__ __forceinline__ int warp_incl_scan(int v) {

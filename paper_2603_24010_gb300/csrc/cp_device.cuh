@@ -62,6 +62,7 @@ struct DevParams {
   double gamma_coef, gamma_max, E_ref_eV, see_scale, T_emit_eV;
   double beam_E_eV, beam_Emin_eV, beam_Emax_eV;
   double beam_ub;        // mono-energetic beam speed sqrt(2 E e / m_i) dt / dx [cells/step]
+  double beam_c0, beam_c1;  // uniform beam: ub^2 = c0 + c1 u (u uniform in [0, 1)) [cells^2/step^2]
   uint64_t seed;
   double scale;          // rho_i = G_i * scale  [C/m^3]
   double kappa[kSpecies];  // q dt^2 / (m dx): cells/step^2 per V/m
@@ -136,6 +137,8 @@ struct DevState {
   double J_pred;              // network's J_hat for the next level [C]
   double err_avg, J_avg;      // running averages of |J - J_hat| and |J|
   int64_t n_eval;             // predictions checked against the realised J
+  double J_eff;               // J_pred while its tracked error is within bound, else 0
+  double pv_phi0, pv_Qsurf;   // phi_0 and Q_surf of the level before the current one
   unsigned long long compact_n[kSpecies];
   unsigned int compact_done;
   uint32_t beam_id_base;
@@ -171,6 +174,7 @@ struct Bufs {
   int64_t hist_rows;
   const double* vs;  // polarity V_s(t_n) for every level n (filled once at set-up)
   const PredNet* net;  // installed predictor, or null
+  int32_t net_in_push;  // 1: the push runs the predictor (FP32 single gap); 0: the solve does
 };
 
 // ---------------------------------------------------------------------------

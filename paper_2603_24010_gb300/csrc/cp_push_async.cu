@@ -14,6 +14,7 @@
 // either end), and the deposit uses one 32-bit sum per node.
 
 #include "cp_common.cuh"
+#include "cp_mlp.cuh"
 
 namespace cpk {
 
@@ -72,6 +73,47 @@ __device__ __forceinline__ float gather_tab(const float* Et, float x) {
 }
 
 constexpr size_t kRingBytes = static_cast<size_t>(kAStages) * kThreads * 32;
+constexpr int kTailRound = kThreads / 4;  // absorbed-ion records per round of the push's tail
+// the tail keeps the beam's node sums (N + 1 <= 11390 words) and the first
+// electrons' draws (2 kTailRound doubles) in the ring
+static_assert(4 * 11392 + 16 * kTailRound <= kRingBytes, "tail scratch lives in the ring");
+static_assert(2 * kTailRound <= kThreads && kTailRound % 32 == 0, "tail roles are whole warps");
+static_assert(sizeof(PredScratch) <= kRingBytes, "predictor scratch lives in the ring");
+static_assert(kThreads >= kHid * 8, "the network takes 8 lanes per neuron");
+
+// The learned weak-coupling predictor for the level the previous solve
+// committed (its row from that level's diagnostics), run by the push's extra
+// CTA (all its threads), with the network read from global memory (L2).
+// Its J_hat is for the level this push starts.
+__device__ __noinline__ void predictor_in_push(DevState* S, const PredNet* net, double C,
+                                               PredScratch* sp) {
+  __shared__ PredLevel L;
+  const int pos0 = ldcg(&S->feat_pos);
+  double v_old = 0.0;
+  if (threadIdx.x < kPredIn - kPredFeat)
+    v_old = ldcg(&S->feat[(pos0 + 1 + static_cast<int>(threadIdx.x) / kPredFeat) & (kPredWindow - 1)]
+                        [threadIdx.x % kPredFeat]);
+  if (threadIdx.x == 0) {
+    L.Qconv = ldcg(&S->cur.Q_conv);
+    L.phi0 = ldcg(&S->cur.V_gap);
+    L.phi0_prev = ldcg(&S->pv_phi0);
+    L.Qsurf = ldcg(&S->cur.Q_surf);
+    L.Qsurf_prev = ldcg(&S->pv_Qsurf);
+    L.Qn = ldcg(&S->cur.Q_circ);
+    L.Q1 = ldcg(&S->Qh[1]);
+    L.emitted = static_cast<double>(ldcg(&S->cur.emitted[0]));
+    L.ion_eV = ldcg(&S->cur.ion_energy_eV);
+    L.had_pred = ldcg(&S->pred_ready);
+    L.J_pred = ldcg(&S->J_pred);
+    L.err_avg = ldcg(&S->err_avg);
+    L.J_avg = ldcg(&S->J_avg);
+    L.n_eval = ldcg(&S->n_eval);
+    L.pos = pos0;
+    L.n_feat = ldcg(&S->n_feat);
+  }
+  __syncthreads();
+  pred_level(net, C, S, &L, v_old, sp);
+}
 
 size_t push_async_smem_bytes(int N) {
   return kRingBytes + align16(sizeof(long long) * (N + 1)) + align16(sizeof(unsigned int) * (N + 1)) +
@@ -89,10 +131,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
   __shared__ long long s_conv, s_energy;
   __shared__ unsigned int s_cfl;
 
-  cudaGridDependencySynchronize();
-  cudaTriggerProgrammaticLaunchCompletion();
+  // Set-up that needs nothing of the previous kernel runs before the wait for
+  // it: the parameters are written once, and the shared grid sums are this
+  // CTA's own.
+  const int N = P->N;
+  float4* ring = reinterpret_cast<float4*>(smem);  // [stage][x | u][thread]
+  long long* Gs = reinterpret_cast<long long*>(smem + kRingBytes);
+  unsigned int* nd = reinterpret_cast<unsigned int*>(smem + kRingBytes + align16(sizeof(long long) * (N + 1)));
+  float* Et = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(nd) + align16(sizeof(unsigned int) * (N + 1)));
+  for (int k = threadIdx.x; k <= N; k += kThreads) {
+    Gs[k] = 0;
+    nd[k] = 0u;
+  }
   if (threadIdx.x == 0) {
-    s_flag[0] = (ldcg(&S->status) != 0);
     s_flag[1] = 0;
     s_abs_n = 0;
     s_conv = 0;
@@ -101,24 +152,42 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     s_emit[0] = s_emit[1] = 0ULL;
   }
   if (threadIdx.x < 2 * kSpecies) s_cnt[threadIdx.x / kSpecies][threadIdx.x % kSpecies] = 0ULL;
-  __syncthreads();
-  if (s_flag[0]) return;
 
-  const int N = P->N;
-  const int64_t step = S->level;
-  float4* ring = reinterpret_cast<float4*>(smem);  // [stage][x | u][thread]
-  long long* Gs = reinterpret_cast<long long*>(smem + kRingBytes);
-  unsigned int* nd = reinterpret_cast<unsigned int*>(smem + kRingBytes + align16(sizeof(long long) * (N + 1)));
-  float* Et = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(nd) + align16(sizeof(unsigned int) * (N + 1)));
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  if (threadIdx.x == 0) s_flag[0] = (ldcg(&S->status) != 0);
+  // the field table of the solve just finished: eight loads per thread in
+  // flight together (one L2 round trip for N <= 4095)
   const float2* Epair = reinterpret_cast<const float2*>(B.Epair);
-  for (int k = threadIdx.x; k <= N; k += kThreads) {
-    Gs[k] = 0;
-    nd[k] = 0u;
-    const float e = Epair[k].x;  // pair 0 repeats E_{1/2}
-    Et[k] = e;
-    if (k == N) Et[N + 1] = e;
+  for (int k0 = threadIdx.x; k0 <= N; k0 += 8 * kThreads) {
+    float e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + q * kThreads;
+      e[q] = (k <= N) ? Epair[k].x : 0.0f;  // pair 0 repeats E_{1/2}
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + q * kThreads;
+      if (k <= N) {
+        Et[k] = e[q];
+        if (k == N) Et[N + 1] = e[q];
+      }
+    }
   }
   __syncthreads();
+  if (s_flag[0]) return;
+  const int64_t step = S->level;
+  // With a network installed the launch has one CTA more, which runs the
+  // learned predictor for the level the previous solve committed (levels
+  // >= 1).  Scheduled last, it takes the first slot a pushing CTA frees, so
+  // the network runs beside the other CTAs' ends.
+  const bool pred_cta = (B.net != nullptr && B.net_in_push);
+  const unsigned int G = gridDim.x - (pred_cta ? 1u : 0u);  // pushing CTAs
+  if (blockIdx.x == G) {
+    if (do_push && step >= 1) predictor_in_push(S, B.net, P->C, reinterpret_cast<PredScratch*>(smem));
+    return;
+  }
 
   const bool half = (S->pushed == 0);
   const float Nr = static_cast<float>(N);
@@ -133,13 +202,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     const int64_t n = S->n_proc[s];  // multiple of 4
     if (n == 0) continue;  // the same for every thread of the CTA
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    const int mine = (ntiles > blockIdx.x) ? static_cast<int>((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+    const int mine = (ntiles > blockIdx.x) ? static_cast<int>((ntiles - blockIdx.x + G - 1) / G) : 0;
     const long long sign = (s == CP_IONS) ? 1LL : -1LL;
     const float kap = P->kap_f[half ? 0 : 1][s];
     const uint32_t* ids = S->id;
     unsigned int a0 = 0u, a1 = 0u;
     int since = 0;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kTile;
+    const int64_t stride = static_cast<int64_t>(G) * kTile;
     const int64_t base0 = static_cast<int64_t>(blockIdx.x) * kTile + static_cast<int64_t>(threadIdx.x) * kPerThread;
     int64_t b_next = base0;  // first particle of this thread's next tile to fetch
     int st_next = 0;         // its ring slot
@@ -227,16 +296,43 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
   }
   cfl = warp_max_u(cfl);
   if (lane_id() == 0 && cfl) atomicMax(&s_cfl, cfl);
+  // This CTA's share [kb0, kb1) of the step's beam ions.  They carry the
+  // other sign than emitted electrons, so they deposit into node sums of
+  // their own, in the ring (idle now: every copy was waited for).
+  const int Bn = do_push ? P->beam_per_step : 0;
+  const int nbc = (Bn + static_cast<int>(G) - 1) / static_cast<int>(G);
+  const int kb0 = min(Bn, static_cast<int>(blockIdx.x) * nbc);
+  const int kb1 = min(Bn, kb0 + nbc);
+  unsigned int* ndb = reinterpret_cast<unsigned int*>(smem);
+  double* s_v0 = reinterpret_cast<double*>(smem + align16(sizeof(unsigned int) * (N + 1)));
+  double* s_f0 = s_v0 + kTailRound;
+  if (kb1 > kb0)
+    for (int k = threadIdx.x; k <= N; k += kThreads) ndb[k] = 0u;
   __syncthreads();
   if (do_push) {
-    // --- secondary emission from the ions this CTA saw absorbed -----------
+    // --- secondary emission from the ions this CTA saw absorbed, and the beam.
+    // Per round of kTailRound records, three FP64 chains run in different
+    // warps: the SE counts (threads [0, kTailRound), from the bottom), the
+    // beam ions (the same threads, from the top) and the first emitted
+    // electron's draws of each record (threads [kTailRound, 2 kTailRound)).
     const int n_abs = s_abs_n;
     if (n_abs > cap && threadIdx.x == 0) s_flag[1] = 1;
     const int na = min(n_abs, cap);
+    const int nb = kb1 - kb0;
     const double dx = P->dx, dt = P->dt;
-    for (int r0 = 0; r0 < na; r0 += kThreads) {
-      const int r = r0 + threadIdx.x;
-      const bool act = r < na;
+    const int rounds = max((na + kTailRound - 1) / kTailRound, (nb + kTailRound - 1) / kTailRound);
+    const int64_t ion_base = S->n_proc[CP_IONS];  // == n_alloc at the push's start
+    const bool counter = threadIdx.x < kTailRound;  // warp-uniform roles
+    const bool drawer = !counter && threadIdx.x < 2 * kTailRound;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int t = static_cast<int>(threadIdx.x) % kTailRound;
+      const int r = rd * kTailRound + t;
+      if (drawer && r < na) {  // the first electron's speed and fraction of the step
+        double f0;
+        s_v0[t] = see_speed(P, my_abs[r].id, step, 0, &f0);
+        s_f0[t] = f0;
+      }
+      const bool act = counter && r < na;
       int nse = 0;
       AbsRec rec;
       rec.id = 0; rec.electrode = 0; rec.u = 0.0;
@@ -253,94 +349,74 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
         }
         if (nse) atomicAdd(&s_emit[rec.electrode], static_cast<unsigned long long>(nse));
       }
-      const int incl = warp_incl_scan(nse);
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      unsigned long long wbase = 0ULL;
-      if (lane_id() == 31 && tot > 0)
-        wbase = atomicAdd(reinterpret_cast<unsigned long long*>(&S->n_alloc[CP_SECONDARIES]),
-                          static_cast<unsigned long long>(tot));
-      wbase = __shfl_sync(0xffffffffu, wbase, 31);
-      if (act && nse > 0) {
-        float* xs = reinterpret_cast<float*>(S->xi[CP_SECONDARIES]);
-        float* us = reinterpret_cast<float*>(S->u[CP_SECONDARIES]);
-        for (int j = 0; j < nse; ++j) {
-          double frac;
-          const double vse = see_speed(P, rec.id, step, j, &frac);
-          const double use = vse * dt / dx;
-          const double xd = (rec.electrode == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(N), __dmul_rn(use, frac));
-          const float xr = nudge_inside<float>(xd, N);
-          const float ur = static_cast<float>(rec.electrode == 0 ? use : -use);
-          const unsigned long long slot = wbase + static_cast<unsigned long long>(incl - nse + j);
-          if (slot < static_cast<unsigned long long>(P->cap[CP_SECONDARIES])) {
-            xs[slot] = xr;
-            us[slot] = ur;
-            deposit_nodes(nd, xr);
-          } else {
-            s_flag[1] = 1;
-          }
-        }
-      }
-      if (P->see_count_law == CP_SEE_COUNT_POISSON) {  // up to 512 x 64 electrons per round
-        __syncthreads();
-        fold_nodes(nd, Gs, N, -1LL);
-        __syncthreads();
-      }
-    }
-    __syncthreads();
-    if (na > 0) {  // floor + Bernoulli: at most 4096 impacts x 15 electrons, no 32-bit overflow
-      fold_nodes(nd, Gs, N, -1LL);
-      __syncthreads();
-    }
-
-    // --- beam ions entering at x = d during this step ----------------------
-    const int Bn = P->beam_per_step;
-    if (Bn > 0 && static_cast<int>(blockIdx.x) * kThreads < Bn) {
-      float* xs = reinterpret_cast<float*>(S->xi[CP_IONS]);
-      float* us = reinterpret_cast<float*>(S->u[CP_IONS]);
-      uint32_t* idw = S->id;
-      const uint32_t id0 = S->beam_id_base;
-      int sincef = 0;
-      for (int k0 = blockIdx.x * kThreads; k0 < Bn; k0 += gridDim.x * kThreads) {
-        const int kk = k0 + threadIdx.x;
-        const bool act = kk < Bn;
-        const unsigned ball = __ballot_sync(0xffffffffu, act);
-        unsigned long long wbase = 0ULL;
-        if (lane_id() == 0 && ball)
-          wbase = atomicAdd(reinterpret_cast<unsigned long long*>(&S->n_alloc[CP_IONS]),
-                            static_cast<unsigned long long>(__popc(ball)));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (act) {
+      // beam ion kk: entry position N - |u_b| frac, speed -|u_b|, in slot
+      // n_proc + kk (ions are appended by the beam alone, so the slots are
+      // known without a shared counter; n_alloc grows by Bn at the end)
+      const int kk = kb0 + rd * kTailRound + (kTailRound - 1 - t);
+      if (counter) {
+        if (kk < kb1) {
           const U64x4 wv = philox4x64_10(static_cast<uint64_t>(kk), static_cast<uint64_t>(step), 0,
                                          0, P->seed, kTagBeam);
           const double frac = u01(wv.w[0]);
-          double ub = P->beam_ub;  // mono-energetic: sqrt(2 E e / m_i) dt / dx, formed on the host
-          if (P->beam_mode != 0) {
-            const double Eb = __dadd_rn(P->beam_Emin_eV,
-                                        __dmul_rn(__dsub_rn(P->beam_Emax_eV, P->beam_Emin_eV), u01(wv.w[1])));
-            ub = sqrt(2.0 * Eb * P->e / P->m_i) * dt / dx;
-          }
+          const double ub = beam_speed_fp32(P, u01(wv.w[1]));
           const float xr = nudge_inside<float>(__dsub_rn(static_cast<double>(N), __dmul_rn(ub, frac)), N);
-          const unsigned long long slot =
-              wbase + static_cast<unsigned long long>(__popc(ball & ((1u << lane_id()) - 1u)));
+          const unsigned long long slot = static_cast<unsigned long long>(ion_base + kk);
           if (slot < static_cast<unsigned long long>(P->cap[CP_IONS])) {
-            xs[slot] = xr;
-            us[slot] = static_cast<float>(-ub);
-            idw[slot] = id0 + static_cast<uint32_t>(step * Bn + kk);
-            deposit_nodes(nd, xr);
+            reinterpret_cast<float*>(S->xi[CP_IONS])[slot] = xr;
+            reinterpret_cast<float*>(S->u[CP_IONS])[slot] = static_cast<float>(-ub);
+            S->id[slot] = S->beam_id_base + static_cast<uint32_t>(step * Bn + kk);
+            deposit_nodes(ndb, xr);
           } else {
             s_flag[1] = 1;
           }
         }
-        if (++sincef == 4 * kFlushTiles) {  // 512 ions per pass: bounded node sums
-          __syncthreads();
-          fold_nodes(nd, Gs, N, 1LL);
-          __syncthreads();
-          sincef = 0;
+      }
+      __syncthreads();  // the first electrons' draws are in shared memory
+      if (counter) {
+        const int incl = warp_incl_scan(nse);
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long wbase = 0ULL;
+        if (lane_id() == 31 && tot > 0)
+          wbase = atomicAdd(reinterpret_cast<unsigned long long*>(&S->n_alloc[CP_SECONDARIES]),
+                            static_cast<unsigned long long>(tot));
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        if (act && nse > 0) {
+          float* xs = reinterpret_cast<float*>(S->xi[CP_SECONDARIES]);
+          float* us = reinterpret_cast<float*>(S->u[CP_SECONDARIES]);
+          for (int j = 0; j < nse; ++j) {
+            double frac, vse;
+            if (j == 0) {
+              vse = s_v0[t];
+              frac = s_f0[t];
+            } else {
+              vse = see_speed(P, rec.id, step, j, &frac);
+            }
+            const double use = vse * dt / dx;
+            const double xd = (rec.electrode == 0) ? __dmul_rn(use, frac) : __dsub_rn(static_cast<double>(N), __dmul_rn(use, frac));
+            const float xr = nudge_inside<float>(xd, N);
+            const float ur = static_cast<float>(rec.electrode == 0 ? use : -use);
+            const unsigned long long slot = wbase + static_cast<unsigned long long>(incl - nse + j);
+            if (slot < static_cast<unsigned long long>(P->cap[CP_SECONDARIES])) {
+              xs[slot] = xr;
+              us[slot] = ur;
+              deposit_nodes(nd, xr);
+            } else {
+              s_flag[1] = 1;
+            }
+          }
         }
       }
+      // per round at most kTailRound x 64 electrons and kTailRound beam ions
+      // per node sum: below 2^32 with a fold between rounds
       __syncthreads();
-      fold_nodes(nd, Gs, N, 1LL);
+      if (rd + 1 < rounds) {
+        if (na > 0) fold_nodes(nd, Gs, N, -1LL);
+        if (nb > 0) fold_nodes(ndb, Gs, N, 1LL);
+        __syncthreads();
+      }
     }
+    if (na > 0) fold_nodes(nd, Gs, N, -1LL);
+    if (nb > 0) fold_nodes(ndb, Gs, N, 1LL);
   }
   __syncthreads();
 
@@ -364,8 +440,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_push_async(Bufs B, int
     if (s_energy) atomicAdd(reinterpret_cast<unsigned long long*>(&S->ion_energy_q),
                             static_cast<unsigned long long>(s_energy));
     if (s_cfl) atomicMax(&S->max_cfl_bits, s_cfl);
-    if (blockIdx.x == 0 && P->beam_per_step > 0)
+    if (blockIdx.x == 0 && P->beam_per_step > 0) {
       atomicAdd(&S->injected, static_cast<unsigned long long>(P->beam_per_step));
+      atomicAdd(reinterpret_cast<unsigned long long*>(&S->n_alloc[CP_IONS]),
+                static_cast<unsigned long long>(P->beam_per_step));
+    }
     if (s_flag[1]) atomicCAS(&S->status, 0, CP_ERR_CAPACITY);
   }
 }
@@ -381,7 +460,8 @@ cudaError_t push_async_occupancy(size_t smem, int* blocks_per_sm) {
 
 cudaError_t push_async_launch(const Bufs& B, int grid, size_t smem, cudaStream_t st, int do_push) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
+  // one CTA more runs the learned predictor when the push carries it
+  cfg.gridDim = dim3(grid + ((B.net != nullptr && B.net_in_push) ? 1 : 0), 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;

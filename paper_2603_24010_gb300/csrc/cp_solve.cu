@@ -312,19 +312,15 @@ __device__ __forceinline__ void prefetch_net(const PredNet* net, PredNet* s_net)
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Predictor step on one CTA (all threads): append the feature row of the
-// level just solved to the 8-level window (a ring: one row written per
-// level) and, once the window is full, evaluate the network (its copy in
-// shared memory, s_net) for the next level's J_hat.
+// Predictor step on one CTA (all threads), for the paths that keep it in the
+// solve: the level's row from the solve's scalars, then the shared predictor
+// level (check, ring append, network on the copy in shared memory, s_net).
 // (The pointers are passed one by one: a reference to the kernel's parameter
 // block would force a copy of it into local memory for the whole solve.)
 __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, const PredNet* s_net,
                                               const double* sc, bool strict_rlc, double phi0) {
-  __shared__ float x[kPredIn];
-  __shared__ float h1[kHid], h2[kHid], h3[kHid];
-  __shared__ float y[kPredOut];
-  __shared__ double s_row[kPredFeat];
-  __shared__ int s_full;
+  __shared__ PredScratch sp;
+  __shared__ PredLevel L;
   // the 7 older rows of the window (ring slots pos+1..pos+7, oldest first),
   // loaded while thread 0 forms the new row
   const int pos0 = static_cast<int>(sc[37]);
@@ -335,56 +331,27 @@ __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, c
   if (threadIdx.x == 0) {
     double Qn, sigma_n, I;
     level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
-    const double A = P->area;
-    double row[kPredFeat];
-    row[0] = sc[6];                    // Q_conv^n
-    row[1] = phi0 - sc[32];            // phi_0^n - phi_0^{n-1}
-    row[2] = sigma_n * A - sc[7] * A;  // Q_surf^n - Q_surf^{n-1}
-    row[3] = sc[33];                   // secondaries emitted at x = 0
-    row[4] = sc[34];                   // energy of the ions absorbed at x = 0 [eV]
-    // the network's prediction for this level against the realised
-    // J^n = C (phi_0^n - phi_0^{n-1}) - (Q^n - Q^{n-1}) (running averages
-    // loaded with the circuit state at the solve's start)
-    if (sc[31] != 0.0) {
-      const double J = P->C * (phi0 - sc[32]) - (Qn - sc[8]);
-      S->err_avg = sc[45] + (fabs(J - sc[30]) - sc[45]) * kPredAvg;
-      S->J_avg = sc[46] + (fabs(J) - sc[46]) * kPredAvg;
-      S->n_eval = static_cast<long long>(sc[47]) + 1;
-    }
-    const int pos = static_cast<int>(sc[37]);  // read with the circuit state at the solve's start
-    for (int f = 0; f < kPredFeat; ++f) {
-      S->feat[pos][f] = row[f];
-      s_row[f] = row[f];
-    }
-    S->feat_pos = (pos + 1) & (kPredWindow - 1);
-    const int nf = min(static_cast<int>(sc[38]) + 1, kPredWindow);
-    S->n_feat = nf;
-    s_full = (nf == kPredWindow);
+    L.Qconv = sc[6];
+    L.phi0 = phi0;
+    L.phi0_prev = sc[32];
+    L.Qsurf = __dmul_rn(sigma_n, P->area);
+    L.Qsurf_prev = __dmul_rn(sc[7], P->area);
+    L.Qn = Qn;
+    L.Q1 = sc[8];
+    L.emitted = sc[33];
+    L.ion_eV = sc[34];
+    // predictor state loaded with the circuit state at the solve's start
+    L.had_pred = (sc[31] != 0.0);
+    L.J_pred = sc[30];
+    L.err_avg = sc[45];
+    L.J_avg = sc[46];
+    L.n_eval = static_cast<long long>(sc[47]);
+    L.pos = pos0;
+    L.n_feat = static_cast<int>(sc[38]);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies of the network
   __syncthreads();
-  if (!s_full) {
-    if (threadIdx.x == 0) S->pred_ready = 0;
-    return;
-  }
-  if (threadIdx.x < kPredIn) {  // window position j (0 = oldest), feature f
-    const int j = threadIdx.x / kPredFeat, f = threadIdx.x % kPredFeat;
-    const double v = (j == kPredWindow - 1) ? s_row[f] : v_old;
-    x[threadIdx.x] = static_cast<float>(v * s_net->inv_in_scale[f]);
-  }
-  __syncthreads();
-  dense_one<kPredIn, kHid, true>(s_net->W1, s_net->b1, x, h1);
-  __syncthreads();
-  dense_one<kHid, kHid, true>(s_net->W2, s_net->b2, h1, h2);
-  __syncthreads();
-  dense_one<kHid, kHid, true>(s_net->W3, s_net->b3, h2, h3);
-  __syncthreads();
-  dense_one<kHid, kPredOut, false>(s_net->W4, s_net->b4, h3, y);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    S->J_pred = static_cast<double>(s_net->out_scale[1]) * static_cast<double>(y[1]);
-    S->pred_ready = 1;
-  }
+  pred_level(s_net, P->C, S, &L, v_old, &sp);
 }
 
 // The solve of one instance by the CTAs of one cluster (a cluster of one CTA
@@ -432,7 +399,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
 
   cudaTriggerProgrammaticLaunchCompletion();
   // the CTA that will run the network fetches it now, behind the scan
-  const bool runs_net = (B.net != nullptr && do_push && rank == (nr > 1 ? 1 : 0));
+  const bool runs_net = (B.net != nullptr && !B.net_in_push && do_push && rank == (nr > 1 ? 1 : 0));
   if (runs_net) prefetch_net(B.net, &s_net);
   const long long G0 = ldcg(&B.G[0]);
   // G of the next chunk's first row (for the field E_hi of the gather table)
@@ -492,7 +459,10 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     int pred_ready = 0, feat_pos = 0, n_feat = 0;
     long long n_eval = 0;
     double J_pred = 0.0, err_avg = 0.0, J_avg = 0.0, bound = 0.0;
-    if (B.net != nullptr) {
+    double J_fast = 0.0;  // the push formed the usable prediction (FP32 single gap)
+    if (B.net != nullptr && B.net_in_push) {
+      if (mode == 2) J_fast = ldcg(&S->J_eff);
+    } else if (B.net != nullptr) {
       pred_ready = ldcg(&S->pred_ready);
       J_pred = ldcg(&S->J_pred);
       n_eval = ldcg(&S->n_eval);
@@ -504,7 +474,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
     }
     if (!pred_ready) J_pred = 0.0;
     const double J_used =
-        (mode == 2 && pred_ready && n_eval >= kPredMinEval && err_avg <= bound * J_avg) ? J_pred : 0.0;
+        (mode == 2 && pred_ready && n_eval >= kPredMinEval && err_avg <= bound * J_avg) ? J_pred : J_fast;
     double g = 0.0, Qpart = Q1, gam = 0.0, inv_den = 1.0;
     if (P->circuit == CP_CIRCUIT_SERIES_RLC) {
       if (mode == 0) {  // strict: Q^n = K - g phi_0^n (Eqs. Q4_phi_relation, K_def)
@@ -869,6 +839,8 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
       if (!isfinite(Qv[0]) || !isfinite(Qv[1]) || !isfinite(Qv[2]) || !isfinite(Qv[4]))
         status = CP_ERR_NONFINITE;
     }
+    S->pv_phi0 = sc[32];  // the predictor's previous level (phi_0, Q_surf)
+    S->pv_Qsurf = sc[7] * A;
     S->sigma = sigma_n;
     S->phi0_last = phi0;
     S->Qh[3] = Q3;
