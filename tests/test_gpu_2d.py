@@ -8,8 +8,10 @@
 * One push from identical states agrees to FP32 rounding; a coupled run with
   beam and SEE tracks the oracle's V_gap and circuit charge.
 * Results do not depend on how often the store is re-sorted (window and
-  global paths share their arithmetic), and a full-size step keeps the
-  charge and particle ledgers exact.
+  global paths share their arithmetic).  At full size (1024 x 1024 cells,
+  2e7 pairs) the charge and particle ledgers are exact, the grid is the
+  oracle's deposit of the GPU's particles and the fields are the oracle's
+  solve of that grid.
 """
 import numpy as np
 import pytest
@@ -206,7 +208,12 @@ def test_results_do_not_depend_on_the_sort_interval(env):
         np.testing.assert_array_equal(G, hs[0][1])
 
 
-def test_full_size_ledgers(env):
+def test_full_size_ledgers_and_fields(env):
+    """1024 x 1024 cells, 2e7 pairs, 2e4 beam ions per step, 12 steps: the
+    charge and particle ledgers are exact, the charge grid equals the
+    oracle's deposit of the GPU's own particles bit for bit, and the fields
+    equal the oracle's solve of that grid with the GPU's circuit state (the
+    level-0 test's tolerances)."""
     torch, native, gap2d = env
     cfg = W.gap_2d(0, n_pairs=20_000_000)
     cfg["beam_per_step"] = 20000
@@ -214,12 +221,35 @@ def test_full_size_ledgers(env):
     steps = 12
     g = gpu_gap(native, cfg, steps, parts=parts)
     h = g.history()
-    G = g.fields()["G"].copy()
+    f = g.fields()
+    G = f["G"].copy()
+    Nx, Ny = int(cfg["n_cells"]), int(cfg["Ny"])
+    Go = np.zeros((Nx + 1, Ny), dtype=np.int64)
+    for sp, sign in ((native.ELECTRONS, -1), (native.IONS, 1), (native.SECONDARIES, -1)):
+        xi, eta = g.particles(sp)[:2]
+        if xi.size:
+            gap2d.deposit2d(Nx, Ny, xi, eta, sign, Go)
     g.close()
     nl = h["n_live"]
     assert nl[0, 0] == 20_000_000
     np.testing.assert_array_equal(np.diff(nl[:, 1]), -h["absorbed"][1:, :, 1].sum(axis=1) + 20000)
-    G[0] //= 2
-    G[-1] //= 2
-    assert G.sum() == 2**32 * (nl[-1, 1] - nl[-1, 0] - nl[-1, 2])
+    np.testing.assert_array_equal(G, Go)
+    Gh = G.copy()
+    Gh[0] //= 2
+    Gh[-1] //= 2
+    assert Gh.sum() == 2**32 * (nl[-1, 1] - nl[-1, 0] - nl[-1, 2])
     assert np.all(h["residual"] <= 1e-12)
+    # the oracle's solve of the last level from the GPU's grid and circuit state
+    n = steps
+    Qc = h["Q_circ"]
+    Qhist = np.array([Qc[n - 1 - k] if n - 1 - k >= 0 else 0.0 for k in range(4)])
+    rc, phi, Ex, Ey, out = gap2d.solve2d(cfg, 0, G, int(h["conv_count"][n]),
+                                         h["Q_surf"][n - 1] / cfg["area"], Qhist,
+                                         n * cfg["dt"], h["V_gap"][n - 1])
+    assert rc == 0
+    scale = np.abs(phi).max()
+    ex_s = np.abs(Ex).max()
+    np.testing.assert_allclose(f["phi"], phi, rtol=0, atol=2e-5 * scale)
+    np.testing.assert_allclose(f["Ex"], Ex, rtol=0, atol=2e-4 * ex_s)
+    np.testing.assert_allclose(f["Ey"], Ey, rtol=0, atol=2e-4 * ex_s)
+    assert h["V_gap"][n] == pytest.approx(phi[0, 0], rel=1e-9)

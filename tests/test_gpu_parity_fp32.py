@@ -146,3 +146,40 @@ def test_pushed_grid_is_the_deposit_of_the_pushed_particles(nat, orc, seed):
                 orc.deposit(N, x, sign, want)
         np.testing.assert_array_equal(G, want)
     g.close()
+
+
+@pytest.mark.parametrize("beam_mode", [0, 1])
+def test_beam_ions_take_their_computed_slots(nat, orc, beam_mode):
+    """Beam ions of a push are stored at slots n_proc + k in the order of
+    their index k (no shared counter), with ids base + step B + k, and their
+    entry positions and speeds equal the oracle's rounded to FP32 (Sec. 3.2;
+    mono-energetic and uniform beams).  Every CTA takes ceil(B / 304) of them,
+    so B = 1000 spreads them over all CTAs unevenly."""
+    cfg = W.scaled(W.gap_1d_fp64(seed=5), precision=W.FP32, beam_per_step=1000,
+                   weight=1e-30, circuit=orc.OPEN)
+    cfg["beam_mode"] = beam_mode
+    N = cfg["n_cells"]
+    rng = np.random.default_rng(3)
+    n0 = 4001  # not a multiple of 4: the first slot after the padding is n_proc
+    xi = rng.uniform(0.3, N - 0.3, n0)
+    ui = np.zeros(n0)
+    xi, ui = W.as_precision(xi, ui, N, W.FP32)
+    g = nat.Gap(cfg, max_steps=4)
+    g.set_particles(nat.IONS, xi, ui)
+    r = orc.OracleGap(cfg)
+    r.set_particles(orc.IONS, xi, ui)
+    for n in (1, 2):
+        g.step(0, 1)
+        assert r.step(orc.STRICT, 1) == orc.OK
+        gx, gu, gid = g.particles(nat.IONS)
+        rx, ru, rid = r.particles(orc.IONS)
+        B = cfg["beam_per_step"]
+        # the newest B ions of both stores, in index order
+        np.testing.assert_array_equal(gid[-B:], rid[-B:].astype(np.uint32))
+        np.testing.assert_array_equal(np.diff(gid[-B:].astype(np.int64)), np.ones(B - 1))
+        rx32, ru32 = W.as_precision(rx[-B:], ru[-B:], N, W.FP32)
+        np.testing.assert_allclose(gx[-B:], rx32, rtol=2**-23, atol=0)
+        np.testing.assert_allclose(gu[-B:], ru32, rtol=2**-23, atol=0)
+    g.close()
+    r.close()
+
