@@ -419,7 +419,7 @@ def run_ensemble(args, K, Wm):
     return out
 
 
-def ensemble_main(args, config):
+def ensemble_main(args, config, emit=True):
     import torch  # noqa: F401
     from paper_2603_24010_gb300 import native  # noqa: F401
     K = args.steps if args.steps is not None else 10000
@@ -452,11 +452,13 @@ def ensemble_main(args, config):
         "status": {"strict": st["rc"], "weak": r["weak"]["rc"]},
         "particle_steps": st["psteps"],
     }
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 # ---------------------------------------------------------------- 2D gap
-def gap2d_main(args, config):
+def gap2d_main(args, config, emit=True):
     """The 2D planar gap: 1024 x 1024 cells (y periodic), 1e8 macroparticles,
     Gaussian beam; strict coupling; one CUDA-event pass times the steps and a
     second, shorter pass times each kernel group for the roofline."""
@@ -516,7 +518,9 @@ def gap2d_main(args, config):
                                % kn[0]},
         "clocks": clk, "particle_steps": psteps,
     }
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 # ---------------------------------------------------------------- coupling
@@ -670,6 +674,8 @@ def main():
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for a profiler "
                          "run with --profile-from-start off)")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the ensemble and 2D gap figures added to the main line")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the learned-vs-plain weak coupling comparison")
     ap.add_argument("--coupling-train", type=int, default=2048)
@@ -780,10 +786,32 @@ def main():
         "t0_window": {"value": r["psteps_t0"] / (r["ms_t0"] * 1e-3), "ms_per_step": r["ms_t0"] / K,
                       "note": "the same K steps timed from t = 0 (1e7 particles, no impacts yet)"},
     }
+    if world == 1 and not args.no_other_workloads:
+        line["other_workloads"] = other_workloads(args)
     print(json.dumps(line))
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def other_workloads(args):
+    """The ensemble and 2D gap benchmarks at their own default sizes, run
+    after the main line's measurements (their figures ride on the same JSON
+    line; `--workload ensemble` / `--workload gap_2d` print their full lines)."""
+    out = {}
+    for name, fn in (("ensemble", ensemble_main), ("gap_2d", gap2d_main)):
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.pairs = None, None
+        ln = fn(sub, {"parallelism": "1 GPU"}, emit=False)
+        rf = ln["roofline"]
+        out[name] = {"value": ln["value"], "unit": ln["unit"], "steps": ln["steps"],
+                     "ms_per_step": ln["ms_per_step"], "workload": ln["config"]["workload"],
+                     "l2": ln["config"]["l2"], "gpu_launches": ln.get("gpu_launches"),
+                     "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                     "kernel", "peak_source",
+                                                     "bytes_per_particle_step")},
+                     "clocks": ln.get("clocks")}
+    return out
 
 
 if __name__ == "__main__":
