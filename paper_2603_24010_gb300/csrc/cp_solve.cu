@@ -298,16 +298,23 @@ __device__ __forceinline__ void level_charges(const DevParams* P, const double* 
   }
 }
 
-// The installed network is copied into shared memory while the solve scans
-// (16-byte asynchronous copies, waited for only when the network runs), so
-// that its four layers read their weights from shared memory.
-__device__ __forceinline__ void prefetch_net(const PredNet* net, PredNet* s_net) {
+// The installed network and the feature window (8 rows of 5 doubles) are
+// copied into shared memory while the solve scans (asynchronous copies,
+// waited for only when the network runs), so that the predictor reads
+// neither from L2 after the solve's last barrier.
+__device__ __forceinline__ void prefetch_net(const PredNet* net, PredNet* s_net, const DevState* S,
+                                             double* s_feat) {
   const char* src = reinterpret_cast<const char*>(net);
   char* dst = reinterpret_cast<char*>(s_net);
   for (size_t o = 16 * static_cast<size_t>(threadIdx.x); o < kPredNetBytes; o += 16 * kSolveThreads)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
                      static_cast<uint32_t>(__cvta_generic_to_shared(dst + o))),
                  "l"(src + o)
+                 : "memory");
+  if (threadIdx.x < kPredWindow * kPredFeat)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(s_feat + threadIdx.x))),
+                 "l"(&S->feat[0][0] + threadIdx.x)
                  : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -318,16 +325,11 @@ __device__ __forceinline__ void prefetch_net(const PredNet* net, PredNet* s_net)
 // (The pointers are passed one by one: a reference to the kernel's parameter
 // block would force a copy of it into local memory for the whole solve.)
 __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, const PredNet* s_net,
-                                              const double* sc, bool strict_rlc, double phi0) {
+                                              const double* s_feat, const double* sc, bool strict_rlc,
+                                              double phi0) {
   __shared__ PredScratch sp;
   __shared__ PredLevel L;
-  // the 7 older rows of the window (ring slots pos+1..pos+7, oldest first),
-  // loaded while thread 0 forms the new row
   const int pos0 = static_cast<int>(sc[37]);
-  double v_old = 0.0;
-  if (threadIdx.x < kPredIn - kPredFeat)
-    v_old = S->feat[(pos0 + 1 + static_cast<int>(threadIdx.x) / kPredFeat) & (kPredWindow - 1)]
-                   [threadIdx.x % kPredFeat];
   if (threadIdx.x == 0) {
     double Qn, sigma_n, I;
     level_charges(P, sc, strict_rlc, phi0, &Qn, &sigma_n, &I);
@@ -351,6 +353,11 @@ __device__ __noinline__ void predictor_update(const DevParams* P, DevState* S, c
   }
   asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies of the network
   __syncthreads();
+  // the 7 older rows of the window (ring slots pos+1..pos+7, oldest first)
+  double v_old = 0.0;
+  if (threadIdx.x < kPredIn - kPredFeat)
+    v_old = s_feat[((pos0 + 1 + static_cast<int>(threadIdx.x) / kPredFeat) & (kPredWindow - 1)) * kPredFeat +
+                   threadIdx.x % kPredFeat];
   pred_level(s_net, P->C, S, &L, v_old, &sp);
 }
 
@@ -380,6 +387,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   __shared__ unsigned long long tal[11];  // the push's tallies, read early
   __shared__ int s_stop;
   __shared__ __align__(16) PredNet s_net;  // the network, for the CTA that runs it
+  __shared__ __align__(16) double s_feat[kPredWindow * kPredFeat];  // and its feature window
 
   cudaGridDependencySynchronize();  // the push that deposited G has completed
   if (threadIdx.x == 0) s_stop = (ldcg(&S->status) != 0);
@@ -400,7 +408,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   cudaTriggerProgrammaticLaunchCompletion();
   // the CTA that will run the network fetches it now, behind the scan
   const bool runs_net = (B.net != nullptr && !B.net_in_push && do_push && rank == (nr > 1 ? 1 : 0));
-  if (runs_net) prefetch_net(B.net, &s_net);
+  if (runs_net) prefetch_net(B.net, &s_net, S, s_feat);
   const long long G0 = ldcg(&B.G[0]);
   // G of the next chunk's first row (for the field E_hi of the gather table)
   const long long Gnext = (hi < N) ? ldcg(&B.G[hi]) : 0LL;
@@ -783,7 +791,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   // rank's remote reads are done
   cl.barrier_wait(std::move(done_tok));
   if (rank == 1) {  // the predictor runs beside rank 0's commit
-    if (runs_net) predictor_update(B.P, B.S, &s_net, sc, strict_c, phi0_fin);
+    if (runs_net) predictor_update(B.P, B.S, &s_net, s_feat, sc, strict_c, phi0_fin);
     return;
   }
   if (rank != 0) return;
@@ -881,7 +889,7 @@ __device__ __forceinline__ void solve_body(const Bufs& B, int do_push, int mode,
   }
   if (nr == 1 && runs_net) {  // a one-CTA solve runs the predictor itself
     __syncthreads();
-    predictor_update(B.P, B.S, &s_net, sc, strict_c, phi0_fin);
+    predictor_update(B.P, B.S, &s_net, s_feat, sc, strict_c, phi0_fin);
   }
 }
 
