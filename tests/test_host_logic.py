@@ -48,8 +48,9 @@ def test_ensemble_vgap_errors_summary():
 
 
 def test_bench_predictor_study_glue(monkeypatch):
-    """bench.py's predictor study assembles its JSON from the driver's
-    results: run here with stand-ins for the GPU calls (shapes only)."""
+    """bench.py's predictor study assembles its JSON from the results of
+    predictor.py's calls: run here with stand-ins for the GPU calls (shapes
+    only)."""
     import json
     import types
     torch = pytest.importorskip("torch")
