@@ -3,6 +3,8 @@
 Bars: the int64 charge grid is bit-exact on identical particle sets; per-step
 fields within 1e-5 (normwise relative) over the first 100 steps under
 identical random draws; V_gap(t) and I(t) within 0.5 % over a full run.
+Edge cases: gaps of 2-5 cells through ion impacts and emission, the largest
+gaps that fit, the full-size deposit, statuses and non-finite inputs.
 """
 import math
 
@@ -359,3 +361,46 @@ def test_nonfinite_input_is_reported(nat, mode, field, value):
     g2.set_particles(nat.IONS, xi, ui)
     assert nat.cp_step_strict(g2.ctx, 5, 1e-12) == nat.OK
     g2.close()
+
+
+# ------------------------------------------------------------- tiny gaps
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_cells,n_pairs", [(2, 37), (3, 101), (5, 64)])
+def test_tiny_gaps_run_against_the_oracle(nat, orc, precision, n_cells, n_pairs):
+    """Gaps of 2-5 cells (the field table's end copies, both electrodes'
+    doubled nodes and the first and last cells all in play every step), a
+    beam of 3 ions per step and emission, 420 steps from identical
+    particles: every level's charge grid is the deposit of the GPU's own
+    particles, FP64 runs reproduce the oracle's event counts and live
+    counts step by step and its V_gap to rounding order, FP32 runs stay
+    within the FP32 event-shift allowance."""
+    # a 0.5 mm gap: the 20 keV beam reaches the cathode after about 255 steps
+    cfg = W.scaled(W.gap_1d_fp64(seed=6), d=5e-4, n_cells=n_cells, n_pairs=n_pairs,
+                   beam_per_step=3, see_scale=8.0)
+    cfg["area"] = cfg["C"] * cfg["d"] / cfg["eps0"]
+    cfg["weight"] = cfg["n0"] * cfg["d"] * cfg["area"] / n_pairs
+    steps = 420
+    g, r = load_both(nat, orc, cfg, precision, max_steps=steps + 1, compact_every=64)
+    for n in (1, 7, 64, 65, 300, 420):
+        g.step(0, n - g.level)
+        G = g.grid()["G"]
+        want = np.zeros(n_cells + 1, dtype=np.int64)
+        for sp, sign in ((nat.ELECTRONS, -1), (nat.IONS, 1), (nat.SECONDARIES, -1)):
+            x = g.particles(sp)[0]
+            if x.size:
+                orc.deposit(n_cells, x, sign, want)
+        np.testing.assert_array_equal(G, want)
+    assert r.step(orc.STRICT, steps) == orc.OK
+    hg, hr = g.history(), r.history()
+    g.close()
+    r.close()
+    assert hr["absorbed"][:, :, 1].sum() > 300 and hr["emitted"].sum() > 30
+    np.testing.assert_array_equal(hg["injected"], hr["injected"])
+    if precision == 0:
+        for k in ("absorbed", "emitted", "n_live", "conv_count"):
+            np.testing.assert_array_equal(hg[k], hr[k], err_msg=k)
+        assert rel(hg["V_gap"], hr["V_gap"]) < 1e-9
+    else:
+        for k in ("n_live",):
+            assert np.abs(hg[k] - hr[k]).max() <= 3 + 0.02 * np.abs(hr[k]).max()
+        assert rel(hg["V_gap"], hr["V_gap"]) < 5e-3
