@@ -124,11 +124,15 @@ __device__ __forceinline__ void deposit_weights(float x, float y, int Ny, int* i
   *w11 = static_cast<unsigned long long>(wx1) * wy1;
 }
 
-// one corner weight w <= 2^32 into the deposit window's two 32-bit parts
-__device__ __forceinline__ void win_add(unsigned int* Dh, unsigned int* Dl, int d, unsigned long long w) {
-  const unsigned int h = static_cast<unsigned int>(w >> 16), l = static_cast<unsigned int>(w) & 0xFFFFu;
-  if (h) atomicAdd(&Dh[d], h);
-  if (l) atomicAdd(&Dl[d], l);
+// cell (i, j) of a particle and its per-axis weights wx1 = floor(frac(x) 2^16),
+// wy1 = floor(frac(y) 2^16), as deposit_weights forms them
+__device__ __forceinline__ void cell_weights(float x, float y, int* i, int* j, unsigned int* wx1,
+                                             unsigned int* wy1) {
+  const float xf = floorf(x), yf = floorf(y);
+  *i = static_cast<int>(xf);
+  *j = static_cast<int>(yf);
+  *wx1 = __float2uint_rz((x - xf) * 65536.0f);
+  *wy1 = __float2uint_rz((y - yf) * 65536.0f);
 }
 
 __device__ __forceinline__ void atomic_add_i64(long long* p, long long v) {
@@ -156,10 +160,20 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         AbsRec2* __restrict__ abs_all, int abs_cap) {
   __shared__ float Exw[kW2 * kW2];
   __shared__ float Eyw[kW2 * kW2];
-  // deposit window: high and low 16-bit parts of the corner weights; an item
-  // of at most 32768 particles adds at most 32768 x 2^16 = 2^31 to either
-  __shared__ unsigned int Dh[kW2 * kW2];
-  __shared__ unsigned int Dl[kW2 * kW2];
+  // Deposit window, by cell (indexed like its lower corner node): the
+  // particle count n, the sums sx, sy of the per-axis weights wx1, wy1 and
+  // the high bits and low 16 bits of the sum sxy of wx1 wy1 (< 2^32 each).
+  // The four corner weights of a particle are linear in these (A = 2^16):
+  // w00 = A^2 - A wx1 - A wy1 + wx1 wy1, w10 = A wx1 - wx1 wy1,
+  // w01 = A wy1 - wx1 wy1, w11 = wx1 wy1; the flush forms each node's exact
+  // int64 sum from its four cells.  An item of at most 32768 particles keeps
+  // every 32-bit sum below 2^31.
+  extern __shared__ unsigned int cwin[];
+  unsigned int* Cn = cwin;
+  unsigned int* Cx = cwin + kW2 * kW2;
+  unsigned int* Cy = cwin + 2 * kW2 * kW2;
+  unsigned int* Ch = cwin + 3 * kW2 * kW2;
+  unsigned int* Cl = cwin + 4 * kW2 * kW2;
   __shared__ int s_items[2 * kSpecies + 1];  // item offsets: sorted / tail per species
   __shared__ int s_abs_n, s_stop, s_over;
   __shared__ unsigned long long s_cnt[2][kSpecies];
@@ -229,8 +243,7 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         const int gy = wrapi(oy + ly, Ny);  // one wrap: Ny >= the window edge
         Exw[q] = (gx >= 0 && gx < D.Nx) ? D.Ex[static_cast<long long>(gx) * Ny + gy] : 0.0f;
         Eyw[q] = (gx >= 0 && gx <= D.Nx) ? D.Ey[static_cast<long long>(gx) * Ny + gy] : 0.0f;
-        Dh[q] = 0u;
-        Dl[q] = 0u;
+        Cn[q] = Cx[q] = Cy[q] = Ch[q] = Cl[q] = 0u;
       }
       __syncthreads();
     } else {
@@ -316,16 +329,17 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
           uv[q] = un;
           yv[q] = yn;
           wv[q] = wn;
-          int i, j, j1;
-          unsigned long long w00, w10, w01, w11;
-          deposit_weights(xn, yn, Ny, &i, &j, &j1, &w00, &w10, &w01, &w11);
+          int i, j;
+          unsigned int wx1, wy1;
+          cell_weights(xn, yn, &i, &j, &wx1, &wy1);
           const int d00 = win ? win_rel(i, j, ox, oy, Ny) : -1;
           if (d00 >= 0) {
-            const int d10 = d00 + kW2, d01 = d00 + 1, d11 = d10 + 1;
-            win_add(Dh, Dl, d00, w00);
-            win_add(Dh, Dl, d10, w10);
-            win_add(Dh, Dl, d01, w01);
-            win_add(Dh, Dl, d11, w11);
+            const unsigned int xy = wx1 * wy1;  // < 2^32
+            atomicAdd(&Cn[d00], 1u);
+            if (wx1) atomicAdd(&Cx[d00], wx1);
+            if (wy1) atomicAdd(&Cy[d00], wy1);
+            if (xy >> 16) atomicAdd(&Ch[d00], xy >> 16);
+            if (xy & 0xFFFFu) atomicAdd(&Cl[d00], xy & 0xFFFFu);
           } else {
             deposit2_global(D, xn, yn, sign);
           }
@@ -339,8 +353,16 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
     if (win) {  // flush the deposit window into the int64 grid
       __syncthreads();
       for (int q = threadIdx.x; q < kW2 * kW2; q += kThreads2) {
-        const unsigned long long v = (static_cast<unsigned long long>(Dh[q]) << 16) + Dl[q];
-        if (v == 0ULL) continue;
+        const int p = q / kW2, r = q % kW2;
+        constexpr long long A = 65536;
+        auto sxy = [&](int c) { return (static_cast<long long>(Ch[c]) << 16) + static_cast<long long>(Cl[c]); };
+        // w00 of cell (p, r), w10 of (p-1, r), w01 of (p, r-1), w11 of (p-1, r-1)
+        long long v = A * A * static_cast<long long>(Cn[q]) - A * static_cast<long long>(Cx[q]) -
+                      A * static_cast<long long>(Cy[q]) + sxy(q);
+        if (p > 0) v += A * static_cast<long long>(Cx[q - kW2]) - sxy(q - kW2);
+        if (r > 0) v += A * static_cast<long long>(Cy[q - 1]) - sxy(q - 1);
+        if (p > 0 && r > 0) v += sxy(q - kW2 - 1);
+        if (v == 0) continue;
         const int gx = ox + q / kW2;
         const int gy = wrapi(oy + q % kW2, Ny);
         const long long dbl = (gx == 0 || gx == D.Nx) ? 2 : 1;
@@ -996,8 +1018,13 @@ size_t absrec2_bytes() { return sizeof(AbsRec2); }
 int kchunk2() { return kChunk2; }
 int tile2() { return kT2; }
 
+constexpr size_t kCwinBytes = 5 * sizeof(unsigned int) * kW2 * kW2;  // the deposit window's cell sums
+
 cudaError_t push2_occupancy(int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k2_push, kThreads2, 0);
+  const cudaError_t e = cudaFuncSetAttribute(k2_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kCwinBytes));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k2_push, kThreads2, kCwinBytes);
 }
 
 cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* abs, int abs_cap,
@@ -1005,6 +1032,7 @@ cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* a
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kThreads2, 1, 1);
+  cfg.dynamicSmemBytes = kCwinBytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
