@@ -46,8 +46,8 @@ cudaError_t solve_ens_launch(int precision, const Bufs* Ball, int n_inst, size_t
                              cudaStream_t st, int do_push, int mode, double tol);
 cudaError_t status_ens_launch(const Bufs* Ball, int E, int* out, cudaStream_t st);
 cudaError_t push2_occupancy(int* per_sm);
-cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* abs, int abs_cap,
-                         int grid, cudaStream_t st);
+cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, const void* D_host, void* abs,
+                         int abs_cap, int grid, cudaStream_t st);
 cudaError_t sort2_launch(DevState* S, void* D, int T, int s, int sms, cudaStream_t st);
 cudaError_t solve2_fwd_launch(void* D, long long* G1, int Nx, int Ny, cudaStream_t st);
 cudaError_t solve2_modes_launch(void* D, int Nx, int Ny, float c_rhs, const double* E64,
@@ -1785,7 +1785,7 @@ int g2_steps(cp_gap2d* g, int mode, int32_t n_steps, double tol) {
       g->since_sort = 0;
     }
     if (g->timing) CP_TRY(g2_timed(g, 0, &rec));
-    CP_CUDA(cpk::push2_launch(c->dP, c->dS, g->dD, g->abs, g->abs_cap, g->grid, c->stream));
+    CP_CUDA(cpk::push2_launch(c->dP, c->dS, g->dD, &g->hd, g->abs, g->abs_cap, g->grid, c->stream));
     g->launches += 1;
     if (g->timing) CP_TRY(mark_end());
     if (g->timing) CP_TRY(g2_timed(g, 1, &rec));

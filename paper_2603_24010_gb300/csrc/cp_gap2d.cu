@@ -157,7 +157,7 @@ __device__ __forceinline__ void deposit2_global(const Dev2D& D, float x, float y
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads2, 2)
 k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ Dp,
-        AbsRec2* __restrict__ abs_all, int abs_cap) {
+        const __grid_constant__ Dev2D Dc, AbsRec2* __restrict__ abs_all, int abs_cap) {
   __shared__ float Exw[kW2 * kW2];
   __shared__ float Eyw[kW2 * kW2];
   // Deposit window, by cell (indexed like its lower corner node): the
@@ -183,7 +183,10 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
 
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
-  const Dev2D& D = *Dp;
+  // the fields fixed at creation come from the launch parameters; the sort
+  // swaps the y, w buffers and sets n_sorted on the device, so those are read
+  // from the device copy
+  const Dev2D& D = Dc;
   if (threadIdx.x == 0) {
     s_stop = (ldcg(&S->status) != 0);
     s_abs_n = 0;
@@ -197,7 +200,7 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
       s_items[2 * s] = acc;
       acc += D.wi_off[s * (D.T + 1) + D.T];
       s_items[2 * s + 1] = acc;
-      const long long tail = S->n_proc[s] - D.n_sorted[s];
+      const long long tail = S->n_proc[s] - Dp->n_sorted[s];
       acc += static_cast<int>((tail + kChunk2 - 1) / kChunk2);
     }
     s_items[2 * kSpecies] = acc;
@@ -248,13 +251,13 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
       __syncthreads();
     } else {
       const int k = item - s_items[2 * s + 1];
-      p0 = D.n_sorted[s] + static_cast<long long>(k) * kChunk2;
+      p0 = Dp->n_sorted[s] + static_cast<long long>(k) * kChunk2;
       p1 = min(static_cast<long long>(S->n_proc[s]), p0 + kChunk2);
     }
     float* xs = reinterpret_cast<float*>(S->xi[s]);
     float* us = reinterpret_cast<float*>(S->u[s]);
-    float* ys = reinterpret_cast<float*>(D.y[s]);
-    float* ws = reinterpret_cast<float*>(D.w[s]);
+    float* ys = reinterpret_cast<float*>(Dp->y[s]);
+    float* ws = reinterpret_cast<float*>(Dp->w[s]);
     const uint32_t* ids = S->id;
     const float kx = D.kx[half ? 0 : 1][s], ky = D.ky[half ? 0 : 1][s];
     const long long sign = (s == CP_IONS) ? 1LL : -1LL;
@@ -404,8 +407,8 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
                   static_cast<unsigned long long>(nse));
     float* xs = reinterpret_cast<float*>(S->xi[CP_SECONDARIES]);
     float* us = reinterpret_cast<float*>(S->u[CP_SECONDARIES]);
-    float* ys = reinterpret_cast<float*>(D.y[CP_SECONDARIES]);
-    float* ws = reinterpret_cast<float*>(D.w[CP_SECONDARIES]);
+    float* ys = reinterpret_cast<float*>(Dp->y[CP_SECONDARIES]);
+    float* ws = reinterpret_cast<float*>(Dp->w[CP_SECONDARIES]);
     for (int jn = 0; jn < nse; ++jn) {
       double frac;
       const double use = see_speed(P, rec.id, step, jn, &frac) * dt / dx;
@@ -429,8 +432,8 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
   if (Bn > 0) {
     float* xs = reinterpret_cast<float*>(S->xi[CP_IONS]);
     float* us = reinterpret_cast<float*>(S->u[CP_IONS]);
-    float* ys = reinterpret_cast<float*>(D.y[CP_IONS]);
-    float* ws = reinterpret_cast<float*>(D.w[CP_IONS]);
+    float* ys = reinterpret_cast<float*>(Dp->y[CP_IONS]);
+    float* ws = reinterpret_cast<float*>(Dp->w[CP_IONS]);
     uint32_t* idw = S->id;
     const uint32_t id0 = S->beam_id_base;
     const double pi = 3.14159265358979323846;
@@ -1027,8 +1030,8 @@ cudaError_t push2_occupancy(int* per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k2_push, kThreads2, kCwinBytes);
 }
 
-cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* abs, int abs_cap,
-                         int grid, cudaStream_t st) {
+cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, const void* D_host, void* abs,
+                         int abs_cap, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kThreads2, 1, 1);
@@ -1040,7 +1043,7 @@ cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, void* a
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k2_push, P, S, static_cast<const Dev2D*>(D),
-                            static_cast<AbsRec2*>(abs), abs_cap);
+                            *static_cast<const Dev2D*>(D_host), static_cast<AbsRec2*>(abs), abs_cap);
 }
 
 cudaError_t sort2_launch(DevState* S, void* D, int T, int s, int sms, cudaStream_t st) {
