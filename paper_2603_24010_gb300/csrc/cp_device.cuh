@@ -147,7 +147,9 @@ struct DevState {
 
 // Installed predictor network: BF16 weights (raw bits, W[out][in]), FP32
 // biases and scales.
-struct PredNet {
+// Whole 16-byte chunks (alignas pads the size): the solve copies it into
+// shared memory with 16-byte asynchronous copies.
+struct alignas(16) PredNet {
   uint16_t W1[kHid * kPredIn];
   uint16_t W2[kHid * kHid];
   uint16_t W3[kHid * kHid];
@@ -159,7 +161,8 @@ struct PredNet {
   double inv_in_scale[kPredFeat];  // 1 / in_scale, formed on the host
 };
 // bytes of a PredNet as allocated and copied (whole 16-byte chunks)
-constexpr size_t kPredNetBytes = (sizeof(PredNet) + 15) & ~size_t(15);
+constexpr size_t kPredNetBytes = sizeof(PredNet);
+static_assert(kPredNetBytes % 16 == 0, "the network is copied in 16-byte chunks");
 
 struct Bufs {
   const DevParams* P;
