@@ -269,82 +269,130 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         load4(us + base, uv);
         load4(ys + base, yv);
         load4(ws + base, wv);
+        // Fast path, without divergent branches: a live particle whose
+        // stencils lie in the window, that stays inside the gap and whose
+        // deposit lands in the window (the common case).  Every other live
+        // particle is flagged and takes the general path below, on its
+        // unchanged values, with the same arithmetic.
+        unsigned int slow = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float x = xv[q];
-          if (!(x > 0.0f && x < D.Nxf)) continue;  // dead slot
-          const Stencil2 st = stencil2(D, x, yv[q]);
-          float ex, ey;
-          // window origins of the two 2x2 stencils (the window is contiguous in
-          // y, so the corners sit at +1 row / +1 column of their origin)
+          const bool alive = (x > 0.0f && x < D.Nxf);
+          const float xa = alive ? x : 1.0f, ya = alive ? yv[q] : 0.0f;  // defined indices for dead slots
+          const Stencil2 st = stencil2(D, xa, ya);
           const int le = win_rel(st.i, st.j, ox, oy, Ny), lf = win_rel(st.a, st.jj, ox, oy, Ny);
-          if (win && le >= 0 && lf >= 0) {
-            const int e00 = le, e10 = le + (st.i1 - st.i) * kW2;
-            const int f00 = lf, f10 = lf + kW2;
-            ex = bilin(Exw[e00], Exw[e10], Exw[e00 + 1], Exw[e10 + 1], st.t, st.v);
-            ey = bilin(Eyw[f00], Eyw[f10], Eyw[f00 + 1], Eyw[f10 + 1], st.fx, st.vy);
-          } else {
-            const float* Ex = D.Ex;
-            const float* Ey = D.Ey;
-            const long long ri = static_cast<long long>(st.i) * Ny, ri1 = static_cast<long long>(st.i1) * Ny;
-            const long long ra = static_cast<long long>(st.a) * Ny, ra1 = static_cast<long long>(st.a1) * Ny;
-            ex = bilin(__ldg(&Ex[ri + st.j]), __ldg(&Ex[ri1 + st.j]), __ldg(&Ex[ri + st.j1]),
-                       __ldg(&Ex[ri1 + st.j1]), st.t, st.v);
-            ey = bilin(__ldg(&Ey[ra + st.jj]), __ldg(&Ey[ra1 + st.jj]), __ldg(&Ey[ra + st.jj1]),
-                       __ldg(&Ey[ra1 + st.jj1]), st.fx, st.vy);
-          }
+          const bool gw = win && alive && le >= 0 && lf >= 0;
+          const int e00 = gw ? le : 0, e10 = gw ? le + (st.i1 - st.i) * kW2 : 0;
+          const int f00 = gw ? lf : 0, f10 = f00 + kW2;
+          const float ex = bilin(Exw[e00], Exw[e10], Exw[e00 + 1], Exw[e10 + 1], st.t, st.v);
+          const float ey = bilin(Eyw[f00], Eyw[f10], Eyw[f00 + 1], Eyw[f10 + 1], st.fx, st.vy);
           const float un = fmaf(kx, ex, uv[q]);
           const float wn = fmaf(ky, ey, wv[q]);
           const float xn = x + un;
           float yn = yv[q] + wn;
           if (yn < 0.0f) yn += D.Nyf;
           if (yn >= D.Nyf) yn -= D.Nyf;
-          if (!(yn >= 0.0f && yn < D.Nyf)) {  // more than one period in a step (or not finite)
-            yn -= D.Nyf * floorf(yn / D.Nyf);
-            if (!(yn >= 0.0f && yn < D.Nyf)) yn = 0.0f;
-          }
-          cfl = max(cfl, __float_as_uint(fmaxf(fabsf(un), fabsf(wn))));
-          if (!(xn > 0.0f && xn < D.Nxf)) {  // absorbed
-            const int el = (xn <= 0.0f) ? 0 : 1;
-            ++a_cnt[el][s];
-            if (s == CP_IONS) {
-              const int slot = atomicAdd(&s_abs_n, 1);
-              if (slot < abs_cap) {
-                AbsRec2 r;
-                r.id = ids[base + q];
-                r.el = static_cast<uint32_t>(el);
-                r.u = un;
-                r.w = wn;
-                r.eta = yn;
-                r.pad = 0.0f;
-                my_abs[slot] = r;
-              } else {
-                s_over = 1;
-              }
-            }
-            xv[q] = -1.0f;
-            uv[q] = 0.0f;
-            yv[q] = 0.0f;
-            wv[q] = 0.0f;
-            continue;
-          }
-          xv[q] = xn;
-          uv[q] = un;
-          yv[q] = yn;
-          wv[q] = wn;
+          const bool inside = (xn > 0.0f && xn < D.Nxf) && (yn >= 0.0f && yn < D.Nyf);
           int i, j;
           unsigned int wx1, wy1;
-          cell_weights(xn, yn, &i, &j, &wx1, &wy1);
+          cell_weights(inside ? xn : 1.0f, inside ? yn : 0.0f, &i, &j, &wx1, &wy1);
           const int d00 = win ? win_rel(i, j, ox, oy, Ny) : -1;
-          if (d00 >= 0) {
+          const bool good = gw && inside && d00 >= 0;
+          if (good) {
             const unsigned int xy = wx1 * wy1;  // < 2^32
             atomicAdd(&Cn[d00], 1u);
             if (wx1) atomicAdd(&Cx[d00], wx1);
             if (wy1) atomicAdd(&Cy[d00], wy1);
             if (xy >> 16) atomicAdd(&Ch[d00], xy >> 16);
             if (xy & 0xFFFFu) atomicAdd(&Cl[d00], xy & 0xFFFFu);
-          } else {
-            deposit2_global(D, xn, yn, sign);
+            cfl = max(cfl, __float_as_uint(fmaxf(fabsf(un), fabsf(wn))));
+            xv[q] = xn;
+            uv[q] = un;
+            yv[q] = yn;
+            wv[q] = wn;
+          } else if (alive) {
+            slow |= 1u << q;
+          }
+        }
+        if (slow) {  // the general path
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (!((slow >> q) & 1u)) continue;
+            const float x = xv[q];
+            const Stencil2 st = stencil2(D, x, yv[q]);
+            float ex, ey;
+            // window origins of the two 2x2 stencils (the window is contiguous in
+            // y, so the corners sit at +1 row / +1 column of their origin)
+            const int le = win_rel(st.i, st.j, ox, oy, Ny), lf = win_rel(st.a, st.jj, ox, oy, Ny);
+            if (win && le >= 0 && lf >= 0) {
+              const int e00 = le, e10 = le + (st.i1 - st.i) * kW2;
+              const int f00 = lf, f10 = lf + kW2;
+              ex = bilin(Exw[e00], Exw[e10], Exw[e00 + 1], Exw[e10 + 1], st.t, st.v);
+              ey = bilin(Eyw[f00], Eyw[f10], Eyw[f00 + 1], Eyw[f10 + 1], st.fx, st.vy);
+            } else {
+              const float* Ex = D.Ex;
+              const float* Ey = D.Ey;
+              const long long ri = static_cast<long long>(st.i) * Ny, ri1 = static_cast<long long>(st.i1) * Ny;
+              const long long ra = static_cast<long long>(st.a) * Ny, ra1 = static_cast<long long>(st.a1) * Ny;
+              ex = bilin(__ldg(&Ex[ri + st.j]), __ldg(&Ex[ri1 + st.j]), __ldg(&Ex[ri + st.j1]),
+                         __ldg(&Ex[ri1 + st.j1]), st.t, st.v);
+              ey = bilin(__ldg(&Ey[ra + st.jj]), __ldg(&Ey[ra1 + st.jj]), __ldg(&Ey[ra + st.jj1]),
+                         __ldg(&Ey[ra1 + st.jj1]), st.fx, st.vy);
+            }
+            const float un = fmaf(kx, ex, uv[q]);
+            const float wn = fmaf(ky, ey, wv[q]);
+            const float xn = x + un;
+            float yn = yv[q] + wn;
+            if (yn < 0.0f) yn += D.Nyf;
+            if (yn >= D.Nyf) yn -= D.Nyf;
+            if (!(yn >= 0.0f && yn < D.Nyf)) {  // more than one period in a step (or not finite)
+              yn -= D.Nyf * floorf(yn / D.Nyf);
+              if (!(yn >= 0.0f && yn < D.Nyf)) yn = 0.0f;
+            }
+            cfl = max(cfl, __float_as_uint(fmaxf(fabsf(un), fabsf(wn))));
+            if (!(xn > 0.0f && xn < D.Nxf)) {  // absorbed
+              const int el = (xn <= 0.0f) ? 0 : 1;
+              ++a_cnt[el][s];
+              if (s == CP_IONS) {
+                const int slot = atomicAdd(&s_abs_n, 1);
+                if (slot < abs_cap) {
+                  AbsRec2 r;
+                  r.id = ids[base + q];
+                  r.el = static_cast<uint32_t>(el);
+                  r.u = un;
+                  r.w = wn;
+                  r.eta = yn;
+                  r.pad = 0.0f;
+                  my_abs[slot] = r;
+                } else {
+                  s_over = 1;
+                }
+              }
+              xv[q] = -1.0f;
+              uv[q] = 0.0f;
+              yv[q] = 0.0f;
+              wv[q] = 0.0f;
+              continue;
+            }
+            xv[q] = xn;
+            uv[q] = un;
+            yv[q] = yn;
+            wv[q] = wn;
+            int i, j;
+            unsigned int wx1, wy1;
+            cell_weights(xn, yn, &i, &j, &wx1, &wy1);
+            const int d00 = win ? win_rel(i, j, ox, oy, Ny) : -1;
+            if (d00 >= 0) {
+              const unsigned int xy = wx1 * wy1;  // < 2^32
+              atomicAdd(&Cn[d00], 1u);
+              if (wx1) atomicAdd(&Cx[d00], wx1);
+              if (wy1) atomicAdd(&Cy[d00], wy1);
+              if (xy >> 16) atomicAdd(&Ch[d00], xy >> 16);
+              if (xy & 0xFFFFu) atomicAdd(&Cl[d00], xy & 0xFFFFu);
+            } else {
+              deposit2_global(D, xn, yn, sign);
+            }
           }
         }
         store4(xs + base, xv);
