@@ -158,8 +158,10 @@ __device__ __forceinline__ void deposit2_global(const Dev2D& D, float x, float y
 __global__ void __launch_bounds__(kThreads2, 2)
 k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ Dp,
         const __grid_constant__ Dev2D Dc, AbsRec2* __restrict__ abs_all, int abs_cap) {
-  __shared__ float Exw[kW2 * kW2];
-  __shared__ float Eyw[kW2 * kW2];
+  // field window: each node holds its value and that of the next node in y
+  // (one 8-byte load per stencil column)
+  __shared__ float2 Exw[kW2 * kW2];
+  __shared__ float2 Eyw[kW2 * kW2];
   // Deposit window, by cell (indexed like its lower corner node): the
   // particle count n, the sums sx, sy of the per-axis weights wx1, wy1 and
   // the high bits and low 16 bits of the sum sxy of wx1 wy1 (< 2^32 each).
@@ -244,8 +246,10 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         const int lx = q / kW2, ly = q % kW2;
         const int gx = ox + lx;
         const int gy = wrapi(oy + ly, Ny);  // one wrap: Ny >= the window edge
-        Exw[q] = (gx >= 0 && gx < D.Nx) ? D.Ex[static_cast<long long>(gx) * Ny + gy] : 0.0f;
-        Eyw[q] = (gx >= 0 && gx <= D.Nx) ? D.Ey[static_cast<long long>(gx) * Ny + gy] : 0.0f;
+        const int gy1 = wrapi(gy + 1, Ny);
+        const long long r = static_cast<long long>(gx) * Ny;
+        Exw[q] = (gx >= 0 && gx < D.Nx) ? make_float2(D.Ex[r + gy], D.Ex[r + gy1]) : make_float2(0.0f, 0.0f);
+        Eyw[q] = (gx >= 0 && gx <= D.Nx) ? make_float2(D.Ey[r + gy], D.Ey[r + gy1]) : make_float2(0.0f, 0.0f);
         Cn[q] = Cx[q] = Cy[q] = Ch[q] = Cl[q] = 0u;
       }
       __syncthreads();
@@ -285,8 +289,9 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
           const bool gw = win && alive && le >= 0 && lf >= 0;
           const int e00 = gw ? le : 0, e10 = gw ? le + (st.i1 - st.i) * kW2 : 0;
           const int f00 = gw ? lf : 0, f10 = f00 + kW2;
-          const float ex = bilin(Exw[e00], Exw[e10], Exw[e00 + 1], Exw[e10 + 1], st.t, st.v);
-          const float ey = bilin(Eyw[f00], Eyw[f10], Eyw[f00 + 1], Eyw[f10 + 1], st.fx, st.vy);
+          const float2 cx0 = Exw[e00], cx1 = Exw[e10], cy0 = Eyw[f00], cy1 = Eyw[f10];
+          const float ex = bilin(cx0.x, cx1.x, cx0.y, cx1.y, st.t, st.v);
+          const float ey = bilin(cy0.x, cy1.x, cy0.y, cy1.y, st.fx, st.vy);
           const float un = fmaf(kx, ex, uv[q]);
           const float wn = fmaf(ky, ey, wv[q]);
           const float xn = x + un;
@@ -328,8 +333,9 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
             if (win && le >= 0 && lf >= 0) {
               const int e00 = le, e10 = le + (st.i1 - st.i) * kW2;
               const int f00 = lf, f10 = lf + kW2;
-              ex = bilin(Exw[e00], Exw[e10], Exw[e00 + 1], Exw[e10 + 1], st.t, st.v);
-              ey = bilin(Eyw[f00], Eyw[f10], Eyw[f00 + 1], Eyw[f10 + 1], st.fx, st.vy);
+              const float2 cx0 = Exw[e00], cx1 = Exw[e10], cy0 = Eyw[f00], cy1 = Eyw[f10];
+              ex = bilin(cx0.x, cx1.x, cx0.y, cx1.y, st.t, st.v);
+              ey = bilin(cy0.x, cy1.x, cy0.y, cy1.y, st.fx, st.vy);
             } else {
               const float* Ex = D.Ex;
               const float* Ey = D.Ey;
