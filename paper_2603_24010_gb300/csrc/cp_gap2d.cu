@@ -587,8 +587,8 @@ __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
   const float* ys = reinterpret_cast<const float*>(D.y[s]);
   long long b0, b1;
   block_range(S->n_proc[s], &b0, &b1);
-  // warp-uniform trips; lanes of one tile (sorted data: most of a warp)
-  // are counted by one shared-memory atomic
+  // warp-uniform trips; each run of consecutive lanes in one tile (sorted
+  // data: most of a warp) is counted by one shared-memory atomic
   constexpr int U = 4;
   const long long step = static_cast<long long>(blockDim.x) * U;
   for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += step) {
@@ -603,8 +603,12 @@ __global__ void k2_hist(const DevState* S, Dev2D* Dp, int s) {
 #pragma unroll
     for (int c = 0; c < U; ++c) {
       const int t = (x[c] > 0.0f && x[c] < D.Nxf) ? tile_of(D, x[c], y[c]) : -1;
-      const unsigned m = __match_any_sync(0xffffffffu, t);
-      if (t >= 0 && static_cast<int>(lane_id()) == __ffs(m) - 1) atomicAdd(&hist[t], __popc(m));
+      const int tp = __shfl_up_sync(0xffffffffu, t, 1);
+      const bool start = (lane_id() == 0) || (t != tp);
+      const unsigned starts = __ballot_sync(0xffffffffu, start);
+      const unsigned later = starts & ~((2u << lane_id()) - 1u);
+      const int next = later ? __ffs(later) - 1 : 32;
+      if (start && t >= 0) atomicAdd(&hist[t], next - static_cast<int>(lane_id()));
     }
   }
   __syncthreads();
@@ -711,7 +715,7 @@ __global__ void k2_bases(Dev2D* Dp, int s, int G) {
     D.bhist[q] += ts[q / G];
 }
 
-__global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
+__global__ void __launch_bounds__(512, 2) k2_scatter(const DevState* S, Dev2D* Dp, int s) {
   extern __shared__ int cur[];
   const Dev2D& D = *Dp;
   for (int t = threadIdx.x; t < D.T; t += blockDim.x)
@@ -730,7 +734,7 @@ __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
   const bool ions = (s == CP_IONS);
   long long b0, b1;
   block_range(S->n_proc[s], &b0, &b1);
-  constexpr int U = 4;  // warp chunks whose loads are issued together
+  constexpr int U = 2;  // warp chunks whose loads are issued together
   const long long step = static_cast<long long>(blockDim.x) * U;
   for (long long k0 = b0 + (threadIdx.x & ~31u); k0 < b1; k0 += step) {
     float x[U], y[U], u[U], w[U];
@@ -748,13 +752,19 @@ __global__ void k2_scatter(const DevState* S, Dev2D* Dp, int s) {
 #pragma unroll
     for (int c = 0; c < U; ++c) {
       const int t = (x[c] > 0.0f && x[c] < D.Nxf) ? tile_of(D, x[c], y[c]) : -1;
-      const unsigned m = __match_any_sync(0xffffffffu, t);
-      const int leader = __ffs(m) - 1;
+      // runs of consecutive lanes in one tile: the run's first lane reserves
+      // its length, every lane takes the slot of its place in the run
+      const int tp = __shfl_up_sync(0xffffffffu, t, 1);
+      const bool start = (lane_id() == 0) || (t != tp);
+      const unsigned starts = __ballot_sync(0xffffffffu, start);
+      const unsigned later = starts & ~((2u << lane_id()) - 1u);  // run starts after this lane
+      const int next = later ? __ffs(later) - 1 : 32;
+      const int rs = 31 - __clz(starts & ((2u << lane_id()) - 1u));  // this lane's run start
       int base = 0;
-      if (t >= 0 && static_cast<int>(lane_id()) == leader) base = atomicAdd(&cur[t], __popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      if (start && t >= 0) base = atomicAdd(&cur[t], next - static_cast<int>(lane_id()));
+      base = __shfl_sync(0xffffffffu, base, rs);
       if (t < 0) continue;
-      const long long o = static_cast<long long>(base) + __popc(m & ((1u << lane_id()) - 1u));
+      const long long o = static_cast<long long>(base) + (static_cast<int>(lane_id()) - rs);
       if (o >= D.cap[s]) continue;  // the sorted store would not fit (reported by k2_swap)
       xd[o] = x[c];
       ud[o] = u[c];
