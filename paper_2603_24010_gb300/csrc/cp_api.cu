@@ -46,7 +46,7 @@ cudaError_t solve_ens_launch(int precision, const Bufs* Ball, int n_inst, size_t
                              cudaStream_t st, int do_push, int mode, double tol);
 cudaError_t status_ens_launch(const Bufs* Ball, int E, int* out, cudaStream_t st);
 cudaError_t push2_occupancy(int* per_sm);
-cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, const void* D_host, void* abs,
+cudaError_t push2_launch(const DevParams* P, DevState* S, void* D, const void* D_host, void* abs,
                          int abs_cap, int grid, cudaStream_t st);
 cudaError_t sort2_launch(DevState* S, void* D, int T, int s, int sms, cudaStream_t st);
 cudaError_t solve2_fwd_launch(void* D, long long* G1, int Nx, int Ny, cudaStream_t st);

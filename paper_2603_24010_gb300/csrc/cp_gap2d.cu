@@ -157,7 +157,8 @@ __device__ __forceinline__ void deposit2_global(const Dev2D& D, float x, float y
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads2, 2)
 k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ Dp,
-        const __grid_constant__ Dev2D Dc, AbsRec2* __restrict__ abs_all, int abs_cap) {
+        const __grid_constant__ Dev2D Dc, int* __restrict__ item_ctr, AbsRec2* __restrict__ abs_all,
+        int abs_cap) {
   // field window: each node holds its value and that of the next node in y
   // (one 8-byte load per stencil column)
   __shared__ float2 Exw[kW2 * kW2];
@@ -218,7 +219,17 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
   unsigned int a_cnt[2][kSpecies] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
 
   const int n_items = s_items[2 * kSpecies];
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  // Work items are taken from a queue (one atomic ticket per item): items
+  // differ in size (whole and partial tiles, the unsorted tails), and a
+  // fixed round-robin deal left CTAs idle while others finished theirs.
+  // The last CTA out resets the queue for the next launch.
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();  // every thread has read the previous ticket
+    if (threadIdx.x == 0) s_item = atomicAdd(&item_ctr[0], 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
     int s = 0;
     while (item >= s_items[2 * s + 2]) ++s;
     const bool tail = item >= s_items[2 * s + 1];
@@ -426,6 +437,14 @@ k2_push(const DevParams* __restrict__ P, DevState* S, const Dev2D* __restrict__ 
         atomic_add_i64(&D.G2[static_cast<long long>(gx) * Ny + gy], sign * dbl * static_cast<long long>(v));
       }
       __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&item_ctr[1], 1) == static_cast<int>(gridDim.x) - 1) {  // every CTA has left the queue
+      item_ctr[0] = 0;
+      item_ctr[1] = 0;
+      __threadfence();
     }
   }
   // tallies of the absorbed particles
@@ -1094,7 +1113,7 @@ cudaError_t push2_occupancy(int* per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k2_push, kThreads2, kCwinBytes);
 }
 
-cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, const void* D_host, void* abs,
+cudaError_t push2_launch(const DevParams* P, DevState* S, void* D, const void* D_host, void* abs,
                          int abs_cap, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
@@ -1107,7 +1126,8 @@ cudaError_t push2_launch(const DevParams* P, DevState* S, const void* D, const v
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k2_push, P, S, static_cast<const Dev2D*>(D),
-                            *static_cast<const Dev2D*>(D_host), static_cast<AbsRec2*>(abs), abs_cap);
+                            *static_cast<const Dev2D*>(D_host), static_cast<Dev2D*>(D)->item_ctr,
+                            static_cast<AbsRec2*>(abs), abs_cap);
 }
 
 cudaError_t sort2_launch(DevState* S, void* D, int T, int s, int sms, cudaStream_t st) {

@@ -48,6 +48,7 @@ struct Dev2D {
   float2* tw;       // [Ny/2] exp(-2 pi i k/Ny)
   int logNy;
   int use_win;      // 0 when Ny < the window edge (the window would wrap onto itself)
+  int item_ctr[2];  // k2_push's work-item queue: next item, CTAs done (zero between launches)
 };
 
 struct AbsRec2 {
