@@ -8,10 +8,11 @@
 //   every `sort_every` steps, which also drops absorbed particles); each
 //   tile's segment starts on a 16-byte boundary.
 // * k2_push: a persistent grid takes work items of up to 32768 particles of
-//   one tile; the item's field window (the tile plus 4 cells of halo, E_x
-//   and E_y) is staged in shared memory and its charge is deposited into a
-//   pair of shared 32-bit windows (a corner weight w < 2^32 + 1 goes in as
-//   w >> 16 and w & 0xffff) flushed once per item into the int64 grid.
+//   one tile from an atomic queue; the item's field window (the tile plus 4
+//   cells of halo, E_x and E_y, each node paired with its neighbour in y)
+//   is staged in shared memory, and its charge goes into five exact 32-bit
+//   sums per cell (count, sum of wx1, sum of wy1, high and low parts of the
+//   sum of wx1 wy1), from which the flush forms every node's int64 charge.
 //   Particles that left their window since the sort (and the unsorted tail
 //   of emitted electrons and beam ions) gather from and deposit into global
 //   memory directly, with the same arithmetic.
