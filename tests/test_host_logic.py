@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: the workload families the benchmark
-and the predictor study draw from, and the predictor driver's error
-summary.  (The kernels are covered by the -m gpu tests.)"""
+and the predictor study draw from, the predictor driver's error summary,
+and the benchmark's clock sampling, peak and host-name helpers.  (The
+kernels are covered by the -m gpu tests.)"""
 import numpy as np
 import pytest
 
@@ -114,3 +115,63 @@ def test_predictor_study_holds_out_its_evaluation_seeds(monkeypatch):
     with pytest.raises(ValueError):
         bench.coupling_seeds(types.SimpleNamespace(coupling_train=64, coupling_train_full=1,
                                                    coupling_eval=4, coupling_eval_full=1))
+
+
+# ---------------------------------------------------------------- bench.py helpers
+class _FakeProc:
+    """Stands in for the nvidia-smi process of ClockSampler."""
+
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _sampler_with_rows(tmp_path, text):
+    import bench
+    cs = bench.ClockSampler(0)
+    f = open(tmp_path / "clocks.csv", "w+")
+    f.write(text)
+    cs.file, cs.proc = f, _FakeProc()
+    return cs
+
+
+def test_clock_sampler_summarises_rows(tmp_path):
+    """Median SM clock, the highest maximum, and the throttle reasons seen
+    Active in any row; rows that do not parse are skipped."""
+    rows = ("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+            "0, 1980, 2070, 1401.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+            "garbage line\n"
+            "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    out = _sampler_with_rows(tmp_path, rows).stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2055.0
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_reports_why_it_has_no_rows(tmp_path):
+    out = _sampler_with_rows(tmp_path, "").stop()
+    assert out["samples"] == 0 and "no rows" in out["why"]
+
+
+def test_measured_peak_or_fallback(tmp_path, monkeypatch):
+    """The HBM peak comes from MEASURED_PEAKS.json at the repository root
+    when it exists, else the stated 6800 GB/s fallback."""
+    import json
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6778.3, "bf16_tflops": 1900.0}))
+    assert bench.measured_peaks() == (6778.3, "measured")
+
+
+def test_cpu_model_names_the_host():
+    import bench
+    name = bench.cpu_model()
+    assert isinstance(name, str) and name
