@@ -75,24 +75,28 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_dram_bytes_per_particle():
-    """DRAM bytes per particle-step of the push kernel from the committed ncu
-    summary, or None when the kernel sources changed since it was taken."""
+def profiled_push_traffic():
+    """(DRAM bytes per particle-step of the push kernel from the committed
+    ncu summary, None) -- or (None, why) when there is no summary or the
+    kernel sources changed since it was taken."""
     try:
         text = open(PUSH_PROFILE).read()
     except OSError:
-        return None
+        return None, "no committed ncu summary of the push"
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith(("dram_bytes_per_particle_step", "source_sha256")):
             k, v = line.strip().split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256") != kernel_source_hash():
-        return None
+    now = kernel_source_hash()
+    if vals.get("source_sha256") != now:
+        return None, ("the push's sources changed since the committed ncu capture (source hash %s, "
+                      "capture %s); traffic not re-measured" % (now, vals.get("source_sha256")))
     try:
-        return float(vals["dram_bytes_per_particle_step"])
+        return float(vals["dram_bytes_per_particle_step"]), None
     except (KeyError, ValueError):
-        return None
+        return None, "the ncu summary gives no DRAM bytes per particle-step"
+
 
 
 def workload_desc(cfg, K, W_, L0):
@@ -336,7 +340,8 @@ def run_native(args, rank, world):
     sel_ms = float(per_launch_ms[:len(sel)][sel[:len(per_launch_ms)]].sum())
     avg_launch_ms = sel_ms / n_sel
     achieved = bpp * float(live_t[sel].sum()) / (sel_ms * 1e-3) / 1e9
-    dbpp = profiled_dram_bytes_per_particle() if cfg["precision"] == W.FP32 else None
+    dbpp, traffic_why = (profiled_push_traffic() if cfg["precision"] == W.FP32
+                         else (None, "no ncu summary of the FP64 push"))
     traffic = dbpp * float(live_t[sel].sum()) / n_sel if dbpp else None
     smin, smax = float((live * bpp / 2).min()) / 1e6, float((live * bpp / 2).max()) / 1e6
     l2 = ("particle state (x, u) %.0f-%.0f MB over the timed steps, %s the 129 MB L2; no flush"
@@ -349,7 +354,8 @@ def run_native(args, rank, world):
                 e2e_psteps=e2e_psteps, h2d=h2d, d2h=d2h, launches=launches,
                 kernel_ms=kms.tolist(), kernel_n=kn.tolist(), avg_launch_ms=avg_launch_ms,
                 achieved=achieved, peak=peak, peak_kind=peak_kind, clocks=clk, bpp=bpp,
-                n_sel=n_sel, traffic=traffic, l2=l2, impacts=impacts, emitted=emitted,
+                n_sel=n_sel, traffic=traffic, traffic_why=traffic_why, l2=l2, impacts=impacts,
+                emitted=emitted,
                 live_mean=float(live.mean()), ms_t0=ms_t0, psteps_t0=psteps_t0, n_all=n_all)
 
 
@@ -767,6 +773,7 @@ def main():
         "gpu_launches": r["launches"],
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["peak"],
                      "unit": "GB/s", "frac": r["achieved"] / r["peak"], "traffic": r["traffic"],
+                     "traffic_note": r["traffic_why"],
                      "kernel": "k_push_async" if r["cfg"]["precision"] == W.FP32 else "k_push",
                      "peak_source": r["peak_kind"],
                      "avg_launch_ms": r["avg_launch_ms"], "launches_used": r["n_sel"],

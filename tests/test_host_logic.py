@@ -175,3 +175,22 @@ def test_cpu_model_names_the_host():
     import bench
     name = bench.cpu_model()
     assert isinstance(name, str) and name
+
+
+def test_push_traffic_only_from_a_capture_of_the_current_sources(tmp_path, monkeypatch):
+    """The bench reports the push's DRAM traffic from the committed ncu
+    summary only while the kernel sources hash to the value recorded there;
+    otherwise traffic is null and the line says why."""
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", [str(src)])
+    prof = tmp_path / "push.md"
+    monkeypatch.setattr(bench, "PUSH_PROFILE", str(prof))
+    assert bench.profiled_push_traffic()[0] is None  # no summary
+    h = bench.kernel_source_hash()
+    prof.write_text("dram_bytes_per_particle_step: 13.99\nsource_sha256: `%s`\n" % h)
+    assert bench.profiled_push_traffic() == (13.99, None)
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    v, why = bench.profiled_push_traffic()
+    assert v is None and "changed" in why and h in why
